@@ -1,0 +1,221 @@
+/*
+ * flic.h — C ABI of libflic: the data-parallel hot path of FLIC (Fast Lidar Image
+ * Clustering, Hasecke, Hahn & Kummert, arXiv 2003.00575) on one GB300 (sm_103a).
+ *
+ * The path, in the paper's terms:
+ *   1. (optional) spherical projection of an xyz cloud into the range image (§I, Fig. 1);
+ *   2. the neighbour test: the law-of-cosines distance between two range readings
+ *      d1, d2 separated by beam angle alpha (Eq. 2), evaluated through a pre-computed
+ *      per-offset constant (Eq. 3), against the single distance threshold delta
+ *      (§III-B), for row and column offsets 1..S — the paper's Map Connections /
+ *      skip connections (§III-B-2) — with azimuth wrap-around;
+ *   3. connected-component labelling of the resulting pixel graph (§III-B-1);
+ *   4. (optional) the scatter of pixel labels back onto the points (§I, Fig. 1).
+ *
+ * Conventions shared by every entry point
+ *   - Images are row-major, row = laser channel, column = azimuth position (§III).
+ *     Pixel p = r * cols + c.
+ *   - Every pointer named "device" is a CUDA device pointer (or managed memory)
+ *     allocated by the caller; the caller owns it.  Pointers named "host" are
+ *     ordinary host memory, read during the call only.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Every compute call only enqueues work on that stream and returns; results are
+ *     ready once the stream reaches that point.  Only the *_create / *_destroy calls
+ *     and flic_device_status synchronise.
+ *   - Nothing throws across the ABI.  Each call returns a flic_status; on a non-OK
+ *     status flic_last_error() returns a thread-local message describing it.
+ *   - A handle is not thread-safe: use one handle per sensor and per host thread.
+ *
+ * Edge predicate (identical on every path; fixed here so that results are exact):
+ *   valid(x)  :=  x > 0 and x finite            (0, negative, NaN, inf are "no return")
+ *   K         :=  (float)(4 sin^2(alpha / 2))    computed in double on the host
+ *                 (= 2 - 2 cos alpha, the constant of Eq. 3 in cancellation-free form)
+ *   edge(a,b) :=  valid(a) && valid(b) && d2 <= delta2, with, in fp32, round-to-nearest,
+ *                 no fused multiply-add:
+ *                     t = a - b;  d2 = t*t + K*(a*b);  delta2 = delta*delta
+ *   Vertical pair (r,c)-(r+k,c), k = 1..S, r+k < rows:
+ *                 alpha = |elev[r+k] - elev[r]|       (K table Kv[r][k-1])
+ *   Horizontal pair (r,c)-(r,(c+k) mod cols), k = 1..S (no wrap: c+k < cols):
+ *                 alpha = k * az_step                 (K table Kh[r][k-1])
+ * Labels: label[p] = the minimum linear index over p's connected component when p is
+ * valid, -1 otherwise.
+ */
+#ifndef FLIC_H
+#define FLIC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FLIC_ABI_VERSION 1
+
+typedef struct flic_ctx* flic_handle;
+typedef struct flic_batch_ctx* flic_batch;
+
+typedef enum {
+    FLIC_OK = 0,
+    FLIC_ERR_INVALID = 1,     /* bad argument: sizes, NULL pointers, non-finite delta ... */
+    FLIC_ERR_OOM = 2,         /* a device or pinned-host allocation failed */
+    FLIC_ERR_CUDA = 3,        /* a CUDA runtime call failed (message has the CUDA error) */
+    FLIC_ERR_TIMEOUT = 4,     /* a bounded device loop gave up (see flic_device_status) */
+    FLIC_ERR_BUSY = 5,        /* a batch object was given more frames than it holds */
+    FLIC_ERR_UNSUPPORTED = 6  /* valid request this build does not handle (e.g. frame too large) */
+} flic_status;
+
+/* flic_create_ex flags */
+#define FLIC_FLAG_NO_WRAP 0x1u  /* columns do not wrap (sensor covers < 360 deg azimuth) */
+
+/* Largest frame the labeller accepts: rows * cols <= FLIC_MAX_PIXELS, rows <= FLIC_MAX_ROWS. */
+#define FLIC_MAX_PIXELS (1 << 22)
+#define FLIC_MAX_ROWS 1024
+#define FLIC_MAX_SKIP 8
+
+/* ABI version compiled into the library (FLIC_ABI_VERSION of its build). */
+int32_t flic_abi_version(void);
+
+/* Thread-local description of the last non-OK status returned on this thread. */
+const char* flic_last_error(void);
+
+/*
+ * flic_create — build a sensor handle: the per-offset cosine constants of Eq. 3
+ * (§III-B; "pre-calculating the cosine of the given angles") and the projection
+ * boundary tables, resident on the current CUDA device.
+ *   rows, cols        range-image shape, 1 <= rows <= FLIC_MAX_ROWS,
+ *                     rows*cols <= FLIC_MAX_PIXELS
+ *   elevation         host, rows doubles: elevation angle of each row's beam in radians,
+ *                     any order (the channel-angle lookup table of §III-A)
+ *   az_step           radians between adjacent columns (> 0, finite)
+ *   delta             distance threshold in metres (> 0, finite); §III-B uses 0.8
+ *   skip              S, 1..FLIC_MAX_SKIP: offsets 1..S are tested along rows and
+ *                     columns (§III-B-2; S = 1 is the plain 4-neighbourhood)
+ *   out               receives the handle; the handle owns all device memory it uses
+ * Synchronises the device.  Errors: FLIC_ERR_INVALID, FLIC_ERR_OOM, FLIC_ERR_CUDA.
+ */
+flic_status flic_create(int32_t rows, int32_t cols, const double* elevation, double az_step,
+                        float delta, int32_t skip, flic_handle* out);
+
+/* flic_create with FLIC_FLAG_* flags (flags = 0 gives flic_create). */
+flic_status flic_create_ex(int32_t rows, int32_t cols, const double* elevation, double az_step,
+                           float delta, int32_t skip, uint32_t flags, flic_handle* out);
+
+/* Frees everything the handle owns.  Synchronises the device.  NULL is accepted. */
+flic_status flic_destroy(flic_handle h);
+
+/*
+ * flic_get_tables — copy the handle's fp32 constants to host memory (for checking):
+ *   kv, kh   host, rows*skip floats each, [r][k-1] layout; Kv entries with r+k >= rows
+ *            are 0.  Either pointer may be NULL.
+ */
+flic_status flic_get_tables(flic_handle h, float* kv, float* kh);
+
+/*
+ * flic_edges — the neighbour test alone (Eq. 2/3 with Map Connections, §III-B-2):
+ *   range    device, rows*cols fp32 (see valid())
+ *   mask     device, rows*cols uint16: bit (k-1) = horizontal edge (r,c)-(r,(c+k) mod cols),
+ *            bit (8+k-1) = vertical edge (r,c)-(r+k,c), for k = 1..S.
+ * Errors: FLIC_ERR_INVALID (NULL pointer), FLIC_ERR_CUDA.
+ */
+flic_status flic_edges(flic_handle h, const float* range, uint16_t* mask, void* stream);
+
+/*
+ * flic_label — the neighbour test followed by connected-component labelling of the
+ * pixel graph (§III-B, §III-B-1, §III-B-2), one frame:
+ *   range    device, rows*cols fp32, not modified
+ *   labels   device, rows*cols int32, written: min linear index of the component, or -1
+ * The labels buffer is also the kernel's only global working memory; it must not alias
+ * range.  Errors: FLIC_ERR_INVALID, FLIC_ERR_CUDA.  A bounded device loop that gives up
+ * is reported by flic_device_status as FLIC_ERR_TIMEOUT.
+ */
+flic_status flic_label(flic_handle h, const float* range, int32_t* labels, void* stream);
+
+/*
+ * flic_project — spherical projection of a point cloud into the range image (§I: used
+ * when raw ranges are unavailable; §IV-B on one-to-one point/pixel matching):
+ *   xyz          device, n*3 fp32, point i = (x, y, z) at xyz[3i..3i+2], sensor at origin
+ *   n            number of points, 0 <= n < 2^31
+ *   range_out    device, rows*cols fp32, written (0 where no point lands); may be NULL,
+ *                then the handle's own buffer is used (see flic_range_buffer)
+ *   point_pixel  device, n int32, written: pixel index of point i, or -1 when the point
+ *                is invalid (range <= 0 or non-finite) or outside the elevation span
+ * Column c holds azimuth [c*az_step, (c+1)*az_step) measured counter-clockwise from +x;
+ * row boundaries are the midpoints between adjacent beam elevations, the outer rows
+ * extending half a spacing beyond their beam.  Bin membership is decided by exact fp32
+ * sign tests against host-built boundary vectors.  Several points in one pixel: the
+ * smallest range wins, ties to the lower point index; every point still records its
+ * pixel.  Requires rows >= 2 and cols*az_step = 2*pi (full revolution; |error| < 1e-6).
+ * Uses a handle-owned scratch of rows*cols 64-bit keys.
+ * Errors: FLIC_ERR_INVALID, FLIC_ERR_UNSUPPORTED (partial revolution), FLIC_ERR_OOM,
+ * FLIC_ERR_CUDA.
+ */
+flic_status flic_project(flic_handle h, const float* xyz, int64_t n, float* range_out,
+                         int32_t* point_pixel, void* stream);
+
+/* Device pointer of the handle's own range image (allocated on first use), or NULL. */
+float* flic_range_buffer(flic_handle h);
+
+/*
+ * flic_scatter — back-projection of pixel labels onto the points (§I, Fig. 1):
+ *   labels        device, rows*cols int32 (a flic_label result)
+ *   point_pixel   device, n int32 (a flic_project result)
+ *   point_labels  device, n int32, written: labels[point_pixel[i]], or -1 when
+ *                 point_pixel[i] < 0
+ * Errors: FLIC_ERR_INVALID, FLIC_ERR_CUDA.
+ */
+flic_status flic_scatter(flic_handle h, const int32_t* labels, const int32_t* point_pixel,
+                         int64_t n, int32_t* point_labels, void* stream);
+
+/*
+ * Batched labelling (no counterpart in the paper, which labels one frame at a time on one
+ * CPU core): many frames of different sensors labelled by one persistent kernel launch,
+ * replayed from a CUDA graph.  Results are identical to flic_label on each frame.
+ *
+ * flic_batch_create — a batch object holding device descriptors for up to max_frames
+ *   frames and the captured graph.  Synchronises.  Errors: INVALID, OOM, CUDA.
+ * flic_label_batch — label nframes frames:
+ *   hs        host array of nframes handles (may repeat; each frame uses its handle's
+ *             shape, tables, delta and skip)
+ *   ranges    host array of nframes device pointers (frame i: rows_i*cols_i fp32)
+ *   labels    host array of nframes device pointers (frame i: rows_i*cols_i int32)
+ *   The host arrays are read during the call only.  Calls on one batch object are
+ *   serialised on their streams by the object (a call waits until the previous call's
+ *   descriptor upload has finished before rewriting its staging buffer).
+ *   Errors: INVALID, BUSY (nframes > max_frames), CUDA.
+ * flic_batch_destroy — frees the object.  Synchronises.  NULL is accepted.
+ */
+flic_status flic_batch_create(int32_t max_frames, flic_batch* out);
+flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* const* ranges,
+                             int32_t* const* labels, int32_t nframes, void* stream);
+flic_status flic_batch_destroy(flic_batch b);
+
+/*
+ * Launch-shape tuning (no counterpart in the paper).  px_per_cta: target pixels per
+ * thread block strip (the tile of the shared-memory union pass), 0 = built-in default;
+ * threads: threads per block (128..1024, multiple of 32), 0 = default;
+ * cluster: max thread blocks cooperating on one frame (1..16), 0 = default.
+ * flic_set_tuning applies to the handle's single-frame calls, flic_batch_set_tuning to
+ * a batch object.  Results never depend on these values.  Errors: FLIC_ERR_INVALID.
+ */
+flic_status flic_set_tuning(flic_handle h, int32_t px_per_cta, int32_t threads, int32_t cluster);
+flic_status flic_batch_set_tuning(flic_batch b, int32_t px_per_cta, int32_t threads,
+                                  int32_t cluster, int32_t ctas_per_sm);
+
+/*
+ * flic_device_status — synchronise the device, read and (if clear != 0) reset the
+ * handle's device error word.  Returns FLIC_OK or FLIC_ERR_TIMEOUT when a bounded loop
+ * in a kernel gave up since the last reset (labels of that call are then not valid).
+ */
+flic_status flic_device_status(flic_handle h, int32_t clear);
+
+/*
+ * flic_debug_set_iter_limit — set the iteration bound of the handle's device loops
+ * (0 = built-in default).  Used to test the timeout path without a real fault.
+ */
+flic_status flic_debug_set_iter_limit(flic_handle h, int32_t limit);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FLIC_H */

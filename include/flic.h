@@ -67,8 +67,10 @@ typedef enum {
 /* flic_create_ex flags */
 #define FLIC_FLAG_NO_WRAP 0x1u  /* columns do not wrap (sensor covers < 360 deg azimuth) */
 
-/* Largest frame the labeller accepts: rows * cols <= FLIC_MAX_PIXELS, rows <= FLIC_MAX_ROWS. */
-#define FLIC_MAX_PIXELS (1 << 22)
+/* Largest frame the labeller accepts: rows * cols <= FLIC_MAX_PIXELS, rows <= FLIC_MAX_ROWS.
+ * A frame is split into at most 16 full-height column strips of at most 32768 (padded)
+ * pixels each; a shape that does not fit gives FLIC_ERR_UNSUPPORTED from flic_create. */
+#define FLIC_MAX_PIXELS (1 << 19)
 #define FLIC_MAX_ROWS 1024
 #define FLIC_MAX_SKIP 8
 
@@ -200,6 +202,26 @@ flic_status flic_batch_destroy(flic_batch b);
 flic_status flic_set_tuning(flic_handle h, int32_t px_per_cta, int32_t threads, int32_t cluster);
 flic_status flic_batch_set_tuning(flic_batch b, int32_t px_per_cta, int32_t threads,
                                   int32_t cluster, int32_t ctas_per_sm);
+
+/*
+ * flic_plan_info — the handle's single-frame launch shape (no counterpart in the paper):
+ *   info  host, 5 ints: strips (= blocks = cluster size), strip width, shared-memory row
+ *         pitch, shared-memory bytes per block, threads per block.
+ * flic_batch_last_plan — shape of the last flic_label_batch launch:
+ *   info  host, 8 ints: work items, clusters launched (persistent grid), blocks per
+ *         cluster, threads per block, shared-memory bytes per block, strips over all
+ *         frames, frames, 0.
+ */
+flic_status flic_plan_info(flic_handle h, int32_t* info);
+
+/*
+ * flic_plan_frame — the strip split flic_create would choose, computed on the host only
+ * (no CUDA call): info, host, 4 ints: strips, strip width, shared-memory row pitch,
+ * shared-memory bytes per block.  Errors: INVALID, UNSUPPORTED (does not fit).
+ */
+flic_status flic_plan_frame(int32_t rows, int32_t cols, int32_t skip, int32_t px_per_cta,
+                            int32_t max_cluster, int32_t* info);
+flic_status flic_batch_last_plan(flic_batch b, int32_t* info);
 
 /*
  * flic_device_status — synchronise the device, read and (if clear != 0) reset the

@@ -1,0 +1,693 @@
+// flic_api.cu — the C ABI of libflic (include/flic.h): handles, host-built tables, the
+// strip planner, batch objects with CUDA-graph replay, status reporting.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "flic.h"
+#include "flic_internal.h"
+
+namespace flic {
+cudaError_t max_active_clusters(int cluster, int threads, size_t smem, int* out);
+}
+
+namespace {
+
+thread_local std::string g_err;
+
+flic_status fail(flic_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+flic_status cuda_fail(cudaError_t e, const char* what) {
+    flic_status st = e == cudaErrorMemoryAllocation ? FLIC_ERR_OOM : FLIC_ERR_CUDA;
+    return fail(st, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kMaxPaddedStrip = 32768;  // rows * pitch of one strip (16-bit keys, see kernel)
+
+struct Tuning {
+    int px_per_cta = 16384;
+    int threads = 512;
+    int cluster = flic::kMaxCluster;
+    int ctas_per_sm = 0;  // batch only: 0 = as many as fit
+};
+
+struct StripPlan {
+    int nstrips = 0;
+    int strip_w = 0;
+    int pitch_log2 = 0;
+    size_t smem = 0;
+};
+
+int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+int pow2_log2_ceil(int x) {
+    int l = 0;
+    while ((1 << l) < x) ++l;
+    return l;
+}
+
+// Split a rows x cols frame into full-height column strips: about px_target pixels each,
+// at most max_cluster strips, widths a multiple of 4 (aligned vector access), every strip
+// at least `skip` wide when there are several (so an edge crosses at most one border),
+// and rows * pitch <= kMaxPaddedStrip with pitch = next power of two >= max(width, 32).
+bool plan_frame(int R, int C, int S, int px_target, int max_cluster, StripPlan* out) {
+    int n0 = std::max(1, std::min(max_cluster, ceil_div(std::max(1, R * C), std::max(1, px_target))));
+    // preferred strip count first, then more strips, then fewer; for each count a few
+    // widths, so that a narrow last strip can be avoided
+    std::vector<int> counts;
+    for (int n = n0; n <= max_cluster; ++n) counts.push_back(n);
+    for (int n = n0 - 1; n >= 1; --n) counts.push_back(n);
+    for (int n : counts) {
+        for (int extra = 0; extra < 4; ++extra) {
+            int W = ceil_div(C, n);
+            if (n > 1) W = ceil_div(W, 4) * 4 + 4 * extra;
+            else if (extra > 0) break;
+            int n_eff = ceil_div(C, W);
+            if (n_eff > 1) {
+                if (W < S) continue;
+                int last = C - (n_eff - 1) * W;
+                if (last < S) continue;
+            }
+            int sh = std::max(5, pow2_log2_ceil(W));
+            if ((long long)R << sh > kMaxPaddedStrip) continue;
+            out->nstrips = n_eff;
+            out->strip_w = W;
+            out->pitch_log2 = sh;
+            out->smem = flic::strip_smem_bytes(R, sh);
+            return true;
+        }
+    }
+    return false;
+}
+
+int device_max_smem() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+// Largest cluster size the device can schedule for the label kernel (16, else 8, ...).
+int usable_cluster(int want, int threads, size_t smem) {
+    for (int c = want; c >= 1; c /= 2) {
+        int n = 0;
+        if (flic::max_active_clusters(c, threads, smem, &n) == cudaSuccess && n > 0) return c;
+        cudaGetLastError();
+    }
+    return 1;
+}
+
+}  // namespace
+
+struct flic_ctx {
+    int R = 0, C = 0, S = 0;
+    float delta = 0.0f, delta2 = 0.0f;
+    uint32_t flags = 0;
+    int wrap = 1;
+    double az_step = 0.0;
+    int device = 0;
+    float* d_kv = nullptr;
+    float* d_kh = nullptr;
+    std::vector<float> h_kv, h_kh;
+    bool proj_ok = false;
+    float* d_colb = nullptr;
+    float* d_rowb = nullptr;
+    int32_t* d_srow = nullptr;
+    float inv_az_step = 0.0f;
+    unsigned long long* d_keys = nullptr;
+    float* d_range = nullptr;
+    int32_t* d_status = nullptr;
+    int iter_limit = 0;
+    Tuning tune;
+    StripPlan plan;
+    int cluster_cap = flic::kMaxCluster;
+};
+
+struct flic_batch_ctx {
+    int max_frames = 0;
+    int device = 0;
+    flic::FrameDesc* h_frames = nullptr;  // pinned staging
+    flic::ItemDesc* h_items = nullptr;
+    flic::FrameDesc* d_frames = nullptr;
+    flic::ItemDesc* d_items = nullptr;
+    cudaEvent_t done = nullptr;
+    bool pending = false;
+    cudaStream_t cap_stream = nullptr;
+    Tuning tune;
+    std::map<std::tuple<int, int, int, int, int, size_t>, cudaGraphExec_t> graphs;
+    int last_info[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+flic::FrameDesc frame_desc(const flic_ctx* h, const float* range, int32_t* labels,
+                           const StripPlan& pl) {
+    flic::FrameDesc f{};
+    f.range = range;
+    f.labels = labels;
+    f.kv = h->d_kv;
+    f.kh = h->d_kh;
+    f.status = h->d_status;
+    f.rows = h->R;
+    f.cols = h->C;
+    f.skip = h->S;
+    f.delta2 = h->delta2;
+    f.wrap = h->wrap;
+    f.nstrips = pl.nstrips;
+    f.strip_w = pl.strip_w;
+    f.pitch_log2 = pl.pitch_log2;
+    f.iter_limit = h->iter_limit;
+    return f;
+}
+
+// Eq. 3 constants, K = 4 sin^2(alpha/2) = 2 - 2 cos(alpha), in double, rounded once.
+void build_k_tables(int R, const double* elev, double az_step, int S, std::vector<float>& kv,
+                    std::vector<float>& kh) {
+    kv.assign((size_t)R * S, 0.0f);
+    kh.assign((size_t)R * S, 0.0f);
+    for (int r = 0; r < R; ++r) {
+        for (int k = 1; k <= S; ++k) {
+            float v = 0.0f;
+            if (r + k < R) {
+                double alpha = std::fabs(elev[r + k] - elev[r]);
+                double s = std::sin(alpha / 2.0);
+                v = (float)(4.0 * s * s);
+            }
+            double alpha_h = (double)k * az_step;
+            double sh = std::sin(alpha_h / 2.0);
+            kv[(size_t)r * S + k - 1] = v;
+            kh[(size_t)r * S + k - 1] = (float)(4.0 * sh * sh);
+        }
+    }
+}
+
+// Projection boundaries: column c starts at azimuth c*az_step; row bands are bounded by
+// midpoints of adjacent sorted beam elevations, outer bands half a spacing beyond.
+bool build_proj_tables(int R, int C, const double* elev, double az_step, std::vector<float>& colb,
+                       std::vector<float>& rowb, std::vector<int32_t>& srow) {
+    if (R < 2) return false;
+    colb.resize((size_t)2 * C);
+    for (int c = 0; c < C; ++c) {
+        double ang = (double)c * az_step;
+        colb[2 * (size_t)c] = (float)std::cos(ang);
+        colb[2 * (size_t)c + 1] = (float)std::sin(ang);
+    }
+    srow.resize(R);
+    for (int r = 0; r < R; ++r) srow[r] = r;
+    std::stable_sort(srow.begin(), srow.end(), [&](int a, int b) { return elev[a] < elev[b]; });
+    for (int i = 1; i < R; ++i)
+        if (!(elev[srow[i]] > elev[srow[i - 1]])) return false;
+    rowb.resize((size_t)2 * (R + 1));
+    for (int j = 0; j <= R; ++j) {
+        double m;
+        if (j == 0) {
+            double e0 = elev[srow[0]], e1 = elev[srow[1]];
+            m = e0 - (e1 - e0) / 2.0;
+        } else if (j == R) {
+            double e0 = elev[srow[R - 2]], e1 = elev[srow[R - 1]];
+            m = e1 + (e1 - e0) / 2.0;
+        } else {
+            m = (elev[srow[j - 1]] + elev[srow[j]]) / 2.0;
+        }
+        rowb[2 * (size_t)j] = (float)std::cos(m);
+        rowb[2 * (size_t)j + 1] = (float)std::sin(m);
+    }
+    return true;
+}
+
+template <typename T>
+flic_status upload(T** dst, const std::vector<T>& src, const char* what) {
+    cudaError_t e = cudaMalloc((void**)dst, sizeof(T) * std::max<size_t>(1, src.size()));
+    if (e != cudaSuccess) return cuda_fail(e, what);
+    if (!src.empty()) {
+        e = cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, what);
+    }
+    return FLIC_OK;
+}
+
+void free_ctx(flic_ctx* h) {
+    if (!h) return;
+    cudaFree(h->d_kv);
+    cudaFree(h->d_kh);
+    cudaFree(h->d_colb);
+    cudaFree(h->d_rowb);
+    cudaFree(h->d_srow);
+    cudaFree(h->d_keys);
+    cudaFree(h->d_range);
+    cudaFree(h->d_status);
+    delete h;
+}
+
+flic_status replan(flic_ctx* h) {
+    StripPlan pl;
+    int cap = h->tune.cluster;
+    if (!plan_frame(h->R, h->C, h->S, h->tune.px_per_cta, cap, &pl))
+        return fail(FLIC_ERR_UNSUPPORTED, "frame %dx%d (skip %d) does not fit %d strips",
+                    h->R, h->C, h->S, cap);
+    if (pl.nstrips > 1) {
+        int c = usable_cluster(pl.nstrips, h->tune.threads, pl.smem);
+        if (c < pl.nstrips) {
+            if (!plan_frame(h->R, h->C, h->S, h->tune.px_per_cta, c, &pl))
+                return fail(FLIC_ERR_UNSUPPORTED, "frame %dx%d needs a cluster of %d blocks",
+                            h->R, h->C, pl.nstrips);
+        }
+    }
+    h->plan = pl;
+    return FLIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t flic_abi_version(void) { return FLIC_ABI_VERSION; }
+
+const char* flic_last_error(void) { return g_err.c_str(); }
+
+flic_status flic_create(int32_t rows, int32_t cols, const double* elevation, double az_step,
+                        float delta, int32_t skip, flic_handle* out) {
+    return flic_create_ex(rows, cols, elevation, az_step, delta, skip, 0u, out);
+}
+
+flic_status flic_create_ex(int32_t rows, int32_t cols, const double* elevation, double az_step,
+                           float delta, int32_t skip, uint32_t flags, flic_handle* out) {
+    if (!out) return fail(FLIC_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (rows < 1 || cols < 1 || rows > FLIC_MAX_ROWS || (int64_t)rows * cols > FLIC_MAX_PIXELS)
+        return fail(FLIC_ERR_INVALID, "bad shape %d x %d (max rows %d, max pixels %d)", rows,
+                    cols, FLIC_MAX_ROWS, FLIC_MAX_PIXELS);
+    if (!elevation) return fail(FLIC_ERR_INVALID, "elevation is NULL");
+    for (int r = 0; r < rows; ++r)
+        if (!std::isfinite(elevation[r])) return fail(FLIC_ERR_INVALID, "elevation[%d] not finite", r);
+    if (!(az_step > 0.0) || !std::isfinite(az_step))
+        return fail(FLIC_ERR_INVALID, "az_step must be positive and finite");
+    if (!(delta > 0.0f) || !std::isfinite(delta))
+        return fail(FLIC_ERR_INVALID, "delta must be positive and finite");
+    if (skip < 1 || skip > FLIC_MAX_SKIP) return fail(FLIC_ERR_INVALID, "skip must be 1..%d", FLIC_MAX_SKIP);
+    if (flags & ~FLIC_FLAG_NO_WRAP) return fail(FLIC_ERR_INVALID, "unknown flags 0x%x", flags);
+
+    flic_ctx* h = new flic_ctx();
+    h->R = rows;
+    h->C = cols;
+    h->S = skip;
+    h->delta = delta;
+    h->delta2 = delta * delta;
+    h->flags = flags;
+    h->wrap = (flags & FLIC_FLAG_NO_WRAP) ? 0 : 1;
+    h->az_step = az_step;
+    cudaGetDevice(&h->device);
+
+    flic_status st;
+    cudaError_t e = flic::label_kernel_setup((size_t)device_max_smem());
+    if (e != cudaSuccess) { free_ctx(h); return cuda_fail(e, "kernel attributes"); }
+
+    build_k_tables(rows, elevation, az_step, skip, h->h_kv, h->h_kh);
+    if ((st = upload(&h->d_kv, h->h_kv, "Kv table")) != FLIC_OK) { free_ctx(h); return st; }
+    if ((st = upload(&h->d_kh, h->h_kh, "Kh table")) != FLIC_OK) { free_ctx(h); return st; }
+    std::vector<int32_t> zero(1, 0);
+    if ((st = upload(&h->d_status, zero, "status word")) != FLIC_OK) { free_ctx(h); return st; }
+
+    std::vector<float> colb, rowb;
+    std::vector<int32_t> srow;
+    bool full_turn = std::fabs((double)cols * az_step - kTwoPi) < 1e-6;
+    if (full_turn && build_proj_tables(rows, cols, elevation, az_step, colb, rowb, srow)) {
+        if ((st = upload(&h->d_colb, colb, "column boundaries")) != FLIC_OK ||
+            (st = upload(&h->d_rowb, rowb, "row boundaries")) != FLIC_OK ||
+            (st = upload(&h->d_srow, srow, "row order")) != FLIC_OK) {
+            free_ctx(h);
+            return st;
+        }
+        size_t npix = (size_t)rows * cols;
+        if ((e = cudaMalloc((void**)&h->d_keys, npix * sizeof(unsigned long long))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&h->d_range, npix * sizeof(float))) != cudaSuccess) {
+            free_ctx(h);
+            return cuda_fail(e, "projection buffers");
+        }
+        h->proj_ok = true;
+        h->inv_az_step = (float)(1.0 / az_step);
+    }
+    if ((st = replan(h)) != FLIC_OK) { free_ctx(h); return st; }
+    e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) { free_ctx(h); return cuda_fail(e, "flic_create"); }
+    *out = h;
+    return FLIC_OK;
+}
+
+flic_status flic_destroy(flic_handle h) {
+    if (!h) return FLIC_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    free_ctx(h);
+    if (e != cudaSuccess) return cuda_fail(e, "flic_destroy");
+    return FLIC_OK;
+}
+
+flic_status flic_get_tables(flic_handle h, float* kv, float* kh) {
+    if (!h) return fail(FLIC_ERR_INVALID, "NULL handle");
+    if (kv) std::memcpy(kv, h->h_kv.data(), sizeof(float) * h->h_kv.size());
+    if (kh) std::memcpy(kh, h->h_kh.data(), sizeof(float) * h->h_kh.size());
+    return FLIC_OK;
+}
+
+flic_status flic_plan_frame(int32_t rows, int32_t cols, int32_t skip, int32_t px_per_cta,
+                            int32_t max_cluster, int32_t* info) {
+    if (!info || rows < 1 || cols < 1 || skip < 1 || skip > FLIC_MAX_SKIP || px_per_cta < 1 ||
+        max_cluster < 1 || max_cluster > flic::kMaxCluster)
+        return fail(FLIC_ERR_INVALID, "bad argument");
+    StripPlan pl;
+    if (!plan_frame(rows, cols, skip, px_per_cta, max_cluster, &pl))
+        return fail(FLIC_ERR_UNSUPPORTED, "frame %dx%d does not fit %d strips", rows, cols,
+                    max_cluster);
+    info[0] = pl.nstrips;
+    info[1] = pl.strip_w;
+    info[2] = 1 << pl.pitch_log2;
+    info[3] = (int32_t)pl.smem;
+    return FLIC_OK;
+}
+
+flic_status flic_plan_info(flic_handle h, int32_t* info) {
+    if (!h || !info) return fail(FLIC_ERR_INVALID, "NULL argument");
+    info[0] = h->plan.nstrips;
+    info[1] = h->plan.strip_w;
+    info[2] = 1 << h->plan.pitch_log2;
+    info[3] = (int32_t)h->plan.smem;
+    info[4] = h->tune.threads;
+    return FLIC_OK;
+}
+
+flic_status flic_edges(flic_handle h, const float* range, uint16_t* mask, void* stream) {
+    if (!h || !range || !mask) return fail(FLIC_ERR_INVALID, "NULL argument");
+    flic::FrameDesc f = frame_desc(h, range, nullptr, h->plan);
+    cudaError_t e = flic::launch_edges(f, mask, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "flic_edges launch");
+    return FLIC_OK;
+}
+
+flic_status flic_label(flic_handle h, const float* range, int32_t* labels, void* stream) {
+    if (!h || !range || !labels) return fail(FLIC_ERR_INVALID, "NULL argument");
+    if ((const void*)range == (const void*)labels) return fail(FLIC_ERR_INVALID, "range aliases labels");
+    flic::LabelLaunch L{};
+    L.frames = nullptr;
+    L.items = nullptr;
+    L.nitems = 1;
+    L.cluster = h->plan.nstrips;
+    L.single = frame_desc(h, range, labels, h->plan);
+    cudaError_t e = flic::launch_label(L, 1, h->tune.threads, h->plan.smem, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "flic_label launch");
+    return FLIC_OK;
+}
+
+flic_status flic_project(flic_handle h, const float* xyz, int64_t n, float* range_out,
+                         int32_t* point_pixel, void* stream) {
+    if (!h) return fail(FLIC_ERR_INVALID, "NULL handle");
+    if (!h->proj_ok)
+        return fail(FLIC_ERR_UNSUPPORTED,
+                    "projection needs rows >= 2, distinct elevations and cols*az_step = 2 pi");
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(FLIC_ERR_INVALID, "bad point count");
+    if (n > 0 && (!xyz || !point_pixel)) return fail(FLIC_ERR_INVALID, "NULL argument");
+    flic::ProjDesc P{};
+    P.colb = h->d_colb;
+    P.rowb = h->d_rowb;
+    P.srow = h->d_srow;
+    P.rows = h->R;
+    P.cols = h->C;
+    P.inv_az_step = h->inv_az_step;
+    P.status = h->d_status;
+    float* out = range_out ? range_out : h->d_range;
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = flic::launch_project(P, xyz, n, h->d_keys, point_pixel, s);
+    if (e == cudaSuccess) e = flic::launch_decode(P, h->d_keys, out, s);
+    if (e != cudaSuccess) return cuda_fail(e, "flic_project launch");
+    return FLIC_OK;
+}
+
+float* flic_range_buffer(flic_handle h) { return h ? h->d_range : nullptr; }
+
+flic_status flic_scatter(flic_handle h, const int32_t* labels, const int32_t* point_pixel,
+                         int64_t n, int32_t* point_labels, void* stream) {
+    if (!h) return fail(FLIC_ERR_INVALID, "NULL handle");
+    if (n < 0) return fail(FLIC_ERR_INVALID, "bad point count");
+    if (n > 0 && (!labels || !point_pixel || !point_labels))
+        return fail(FLIC_ERR_INVALID, "NULL argument");
+    cudaError_t e = flic::launch_scatter(labels, (int64_t)h->R * h->C, point_pixel, n,
+                                         point_labels, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "flic_scatter launch");
+    return FLIC_OK;
+}
+
+flic_status flic_set_tuning(flic_handle h, int32_t px_per_cta, int32_t threads, int32_t cluster) {
+    if (!h) return fail(FLIC_ERR_INVALID, "NULL handle");
+    if (px_per_cta < 0 || threads < 0 || cluster < 0 || cluster > flic::kMaxCluster ||
+        (threads && (threads < 128 || threads > 1024 || threads % 32)))
+        return fail(FLIC_ERR_INVALID, "bad tuning values");
+    Tuning old = h->tune;
+    Tuning def;
+    h->tune.px_per_cta = px_per_cta ? px_per_cta : def.px_per_cta;
+    h->tune.threads = threads ? threads : def.threads;
+    h->tune.cluster = cluster ? cluster : def.cluster;
+    flic_status st = replan(h);
+    if (st != FLIC_OK) {
+        h->tune = old;
+        replan(h);
+    }
+    return st;
+}
+
+flic_status flic_device_status(flic_handle h, int32_t clear) {
+    if (!h) return fail(FLIC_ERR_INVALID, "NULL handle");
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "flic_device_status");
+    int32_t v = 0;
+    e = cudaMemcpy(&v, h->d_status, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "flic_device_status read");
+    if (clear) {
+        int32_t z = 0;
+        e = cudaMemcpy(h->d_status, &z, sizeof(z), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "flic_device_status clear");
+    }
+    if (v != 0) return fail(FLIC_ERR_TIMEOUT, "a bounded device loop gave up (status %d)", v);
+    return FLIC_OK;
+}
+
+flic_status flic_debug_set_iter_limit(flic_handle h, int32_t limit) {
+    if (!h || limit < 0) return fail(FLIC_ERR_INVALID, "bad argument");
+    h->iter_limit = limit;
+    return FLIC_OK;
+}
+
+// ------------------------------------------------------------------------------- batch
+
+flic_status flic_batch_create(int32_t max_frames, flic_batch* out) {
+    if (!out) return fail(FLIC_ERR_INVALID, "out is NULL");
+    *out = nullptr;
+    if (max_frames < 1 || max_frames > (1 << 15))
+        return fail(FLIC_ERR_INVALID, "max_frames must be 1..32768");
+    flic_batch_ctx* b = new flic_batch_ctx();
+    b->max_frames = max_frames;
+    cudaGetDevice(&b->device);
+    cudaError_t e;
+    size_t fb = sizeof(flic::FrameDesc) * (size_t)max_frames;
+    size_t ib = sizeof(flic::ItemDesc) * (size_t)max_frames;
+    if ((e = cudaHostAlloc((void**)&b->h_frames, fb, cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaHostAlloc((void**)&b->h_items, ib, cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&b->d_frames, fb)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&b->d_items, ib)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        flic_batch_destroy(b);
+        return cuda_fail(e, "flic_batch_create");
+    }
+    if ((e = flic::label_kernel_setup((size_t)device_max_smem())) != cudaSuccess) {
+        flic_batch_destroy(b);
+        return cuda_fail(e, "kernel attributes");
+    }
+    *out = b;
+    return FLIC_OK;
+}
+
+static void clear_graphs(flic_batch_ctx* b) {
+    for (auto& kv : b->graphs) cudaGraphExecDestroy(kv.second);
+    b->graphs.clear();
+}
+
+flic_status flic_batch_destroy(flic_batch b) {
+    if (!b) return FLIC_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    clear_graphs(b);
+    if (b->h_frames) cudaFreeHost(b->h_frames);
+    if (b->h_items) cudaFreeHost(b->h_items);
+    cudaFree(b->d_frames);
+    cudaFree(b->d_items);
+    if (b->done) cudaEventDestroy(b->done);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
+    if (e != cudaSuccess) return cuda_fail(e, "flic_batch_destroy");
+    return FLIC_OK;
+}
+
+flic_status flic_batch_set_tuning(flic_batch b, int32_t px_per_cta, int32_t threads,
+                                  int32_t cluster, int32_t ctas_per_sm) {
+    if (!b) return fail(FLIC_ERR_INVALID, "NULL batch");
+    if (px_per_cta < 0 || threads < 0 || cluster < 0 || cluster > flic::kMaxCluster ||
+        ctas_per_sm < 0 || (threads && (threads < 128 || threads > 1024 || threads % 32)))
+        return fail(FLIC_ERR_INVALID, "bad tuning values");
+    if (b->pending) cudaEventSynchronize(b->done);
+    Tuning def;
+    b->tune.px_per_cta = px_per_cta ? px_per_cta : def.px_per_cta;
+    b->tune.threads = threads ? threads : def.threads;
+    b->tune.cluster = cluster ? cluster : def.cluster;
+    b->tune.ctas_per_sm = ctas_per_sm;
+    clear_graphs(b);
+    return FLIC_OK;
+}
+
+flic_status flic_batch_last_plan(flic_batch b, int32_t* info) {
+    if (!b || !info) return fail(FLIC_ERR_INVALID, "NULL argument");
+    std::memcpy(info, b->last_info, sizeof(b->last_info));
+    return FLIC_OK;
+}
+
+flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* const* ranges,
+                             int32_t* const* labels, int32_t nframes, void* stream) {
+    if (!b) return fail(FLIC_ERR_INVALID, "NULL batch");
+    if (nframes < 0) return fail(FLIC_ERR_INVALID, "nframes < 0");
+    if (nframes == 0) return FLIC_OK;
+    if (nframes > b->max_frames)
+        return fail(FLIC_ERR_BUSY, "%d frames > batch capacity %d", nframes, b->max_frames);
+    if (!hs || !ranges || !labels) return fail(FLIC_ERR_INVALID, "NULL argument");
+    for (int i = 0; i < nframes; ++i) {
+        if (!hs[i] || !ranges[i] || !labels[i])
+            return fail(FLIC_ERR_INVALID, "frame %d: NULL handle or buffer", i);
+        if ((const void*)ranges[i] == (const void*)labels[i])
+            return fail(FLIC_ERR_INVALID, "frame %d: range aliases labels", i);
+    }
+    if (b->pending) {
+        cudaError_t e = cudaEventSynchronize(b->done);
+        if (e != cudaSuccess) return cuda_fail(e, "waiting for the previous batch");
+        b->pending = false;
+    }
+    const Tuning& t = b->tune;
+
+    // cluster size this device schedules at the largest strip footprint
+    std::vector<StripPlan> plans(nframes);
+    size_t smem = 0;
+    int cluster = t.cluster;
+    for (int pass = 0; pass < 2; ++pass) {
+        smem = 0;
+        for (int i = 0; i < nframes; ++i) {
+            const flic_ctx* h = hs[i];
+            if (!plan_frame(h->R, h->C, h->S, t.px_per_cta, cluster, &plans[i]))
+                return fail(FLIC_ERR_UNSUPPORTED, "frame %d (%dx%d) does not fit %d strips", i,
+                            h->R, h->C, cluster);
+            smem = std::max(smem, plans[i].smem);
+        }
+        int c = usable_cluster(cluster, t.threads, smem);
+        if (c == cluster) break;
+        cluster = c;
+    }
+
+    // first-fit decreasing: frames with more strips first, each frame's strips on
+    // consecutive ranks of one item
+    std::vector<int> order(nframes);
+    for (int i = 0; i < nframes; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int c) { return plans[a].nstrips > plans[c].nstrips; });
+    std::vector<int> used;  // ranks used per item
+    for (int i = 0; i < nframes; ++i) {
+        b->h_frames[i] = frame_desc(hs[i], ranges[i], labels[i], plans[i]);
+    }
+    for (int oi = 0; oi < nframes; ++oi) {
+        const int fi = order[oi];
+        const int ns = plans[fi].nstrips;
+        size_t it = 0;
+        while (it < used.size() && used[it] + ns > cluster) ++it;
+        if (it == used.size()) {
+            used.push_back(0);
+            flic::ItemDesc& d = b->h_items[it];
+            for (int q = 0; q < flic::kMaxCluster; ++q) {
+                d.frame[q] = -1;
+                d.strip[q] = 0;
+            }
+        }
+        flic::ItemDesc& d = b->h_items[it];
+        for (int s = 0; s < ns; ++s) {
+            d.frame[used[it] + s] = (int16_t)fi;
+            d.strip[used[it] + s] = (int16_t)s;
+        }
+        used[it] += ns;
+    }
+    const int nitems = (int)used.size();
+
+    int active = 0;
+    cudaError_t e = flic::max_active_clusters(cluster, t.threads, smem, &active);
+    if (e != cudaSuccess || active < 1) {
+        cudaGetLastError();
+        return fail(FLIC_ERR_UNSUPPORTED, "no cluster of %d blocks with %zu B shared memory fits",
+                    cluster, smem);
+    }
+    if (t.ctas_per_sm > 0) {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        active = std::max(1, std::min(active, nsm * t.ctas_per_sm / cluster));
+    }
+    const int grid = std::min(nitems, active);
+
+    auto key = std::make_tuple(nframes, nitems, grid, cluster, t.threads, smem);
+    auto found = b->graphs.find(key);
+    cudaGraphExec_t exec = nullptr;
+    if (found != b->graphs.end()) {
+        exec = found->second;
+    } else {
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture begin");
+        cudaMemcpyAsync(b->d_frames, b->h_frames, sizeof(flic::FrameDesc) * nframes,
+                        cudaMemcpyHostToDevice, b->cap_stream);
+        cudaMemcpyAsync(b->d_items, b->h_items, sizeof(flic::ItemDesc) * nitems,
+                        cudaMemcpyHostToDevice, b->cap_stream);
+        flic::LabelLaunch L{};
+        L.frames = b->d_frames;
+        L.items = b->d_items;
+        L.nitems = nitems;
+        L.cluster = cluster;
+        cudaError_t le = flic::launch_label(L, grid, t.threads, smem, b->cap_stream);
+        e = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (le != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return cuda_fail(le, "batch kernel capture");
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "graph capture end");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "graph instantiate");
+        b->graphs[key] = exec;
+    }
+    e = cudaGraphLaunch(exec, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+    e = cudaEventRecord(b->done, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "event record");
+    b->pending = true;
+    int total_ctas = 0;
+    for (int i = 0; i < nframes; ++i) total_ctas += plans[i].nstrips;
+    int info[8] = {nitems, grid, cluster, t.threads, (int)smem, total_ctas, nframes, 0};
+    std::memcpy(b->last_info, info, sizeof(info));
+    return FLIC_OK;
+}
+
+}  // extern "C"

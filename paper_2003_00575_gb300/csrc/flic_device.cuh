@@ -1,0 +1,140 @@
+// flic_device.cuh — device helpers shared by the FLIC kernels.
+#pragma once
+
+#include <cstdint>
+
+#include "flic_internal.h"
+
+namespace flic {
+
+constexpr float kFltMax = 3.402823466e+38f;
+constexpr int32_t kStatusTimeout = 4;  // == FLIC_ERR_TIMEOUT
+
+// A range reading is a measurement iff positive and finite (zero = no return, §III-A).
+__device__ __forceinline__ bool valid_range(float x) { return x > 0.0f && x <= kFltMax; }
+
+// Read-only load of one range reading; anything that is not a measurement becomes 0.
+__device__ __forceinline__ float load_range(const float* p) {
+    float x = __ldg(p);
+    return valid_range(x) ? x : 0.0f;
+}
+
+// Eq. 2 squared in the form (a - b)^2 + K (a b), K = 2 - 2 cos(alpha) (Eq. 3's constant
+// without its cancellation), against delta^2.  Every operation is a separately rounded
+// fp32 op (explicit _rn intrinsics are never contracted into an FMA), and K multiplies
+// the product a*b so that the result is symmetric in (a, b) bit for bit.
+__device__ __forceinline__ bool edge_pred(float a, float b, float K, float delta2) {
+    float t = __fsub_rn(a, b);
+    float tt = __fmul_rn(t, t);
+    float ab = __fmul_rn(a, b);
+    float kab = __fmul_rn(K, ab);
+    float d2 = __fadd_rn(tt, kab);
+    return d2 <= delta2;
+}
+
+__device__ __forceinline__ void report_timeout(int32_t* status) {
+    if (status) atomicExch(status, kStatusTimeout);
+}
+
+// ---- union-find in shared memory (tile-local forest, 16-bit local indices) -------------
+// par[x] == x: root; par[x] < x otherwise (hooking always goes to the smaller index, so
+// the root of a set is its minimum element).  Path halving during finds; a store racing
+// with an atomicMin only replaces one ancestor by another, and a union whose atomicMin
+// lost the race retries with the value it found.
+
+__device__ __forceinline__ int find_smem(volatile int* par, int x, int& budget) {
+    while (true) {
+        int p = par[x];
+        if (p == x) return x;
+        int gp = par[p];
+        if (gp == p) return p;
+        par[x] = gp;
+        x = gp;
+        if (--budget <= 0) return x;
+    }
+}
+
+// Read-only find, for the compression pass: once unions are over, each entry is written
+// only by its owner (with its final root), so no stale ancestor can overwrite a root that
+// another thread has just stored (which a halving store issued from an older read could).
+__device__ __forceinline__ int find_smem_ro(const volatile int* par, int x, int& budget) {
+    int p = par[x];
+    while (p != x) {
+        x = p;
+        p = par[x];
+        if (--budget <= 0) break;
+    }
+    return x;
+}
+
+__device__ __forceinline__ void union_smem(int* par, int a, int b, int& budget) {
+    volatile int* vp = par;
+    while (budget > 0) {
+        a = find_smem(vp, a, budget);
+        b = find_smem(vp, b, budget);
+        if (a == b) return;
+        if (a > b) { int t = a; a = b; b = t; }
+        int old = atomicMin(par + b, a);
+        if (old == b) return;
+        b = old;
+        --budget;
+    }
+}
+
+// ---- union-find in global memory (the labels buffer holds the cross-strip forest) ------
+// Loads bypass L1 (.cg): other blocks write these entries.
+
+__device__ __forceinline__ int find_global(int32_t* lab, int x, int& budget, bool compress) {
+    while (true) {
+        int p = __ldcg(lab + x);
+        if (p == x) return x;
+        int gp = __ldcg(lab + p);
+        if (gp == p) return p;
+        if (compress) __stcg(lab + x, gp);
+        x = gp;
+        if (--budget <= 0) return x;
+    }
+}
+
+__device__ __forceinline__ void union_global(int32_t* lab, int a, int b, int& budget) {
+    while (budget > 0) {
+        a = find_global(lab, a, budget, true);
+        b = find_global(lab, b, budget, true);
+        if (a == b) return;
+        if (a > b) { int t = a; a = b; b = t; }
+        int old = atomicMin(lab + b, a);
+        if (old == b) return;
+        b = old;
+        --budget;
+    }
+}
+
+// ---- thread-block cluster helpers -----------------------------------------------------
+
+__device__ __forceinline__ unsigned cluster_ctarank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_index() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ unsigned cluster_count() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+
+// Every thread of every block of the cluster arrives; release/acquire at cluster scope
+// orders the global-memory writes made before it with the reads made after it.
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile(
+        "barrier.cluster.arrive.release;\n\t"
+        "barrier.cluster.wait.acquire;" ::: "memory");
+}
+
+}  // namespace flic

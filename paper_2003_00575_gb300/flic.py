@@ -1,0 +1,284 @@
+"""Thin Python binding of libflic (include/flic.h): argument marshalling only.
+
+Every function has the name of the C entry point it calls.  Device buffers are torch
+tensors on the CUDA device (PyTorch provides memory and streams only); every step of the
+hot path runs in libflic's kernels.  Importing this module loads libflic.so and raises
+if it has not been built (``python -c "import __graft_entry__ as g; g.build()"``):
+there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libflic.so")
+
+FLIC_OK = 0
+FLIC_ERR_INVALID = 1
+FLIC_ERR_OOM = 2
+FLIC_ERR_CUDA = 3
+FLIC_ERR_TIMEOUT = 4
+FLIC_ERR_BUSY = 5
+FLIC_ERR_UNSUPPORTED = 6
+FLIC_FLAG_NO_WRAP = 1
+FLIC_MAX_PIXELS = 1 << 19
+FLIC_MAX_ROWS = 1024
+FLIC_MAX_SKIP = 8
+
+# every symbol include/flic.h declares, with (restype, argtypes)
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_I64 = ctypes.c_int64
+_U32 = ctypes.c_uint32
+_F32 = ctypes.c_float
+_F64 = ctypes.c_double
+SIGNATURES = {
+    "flic_abi_version": (_I32, []),
+    "flic_last_error": (ctypes.c_char_p, []),
+    "flic_create": (_I32, [_I32, _I32, _P, _F64, _F32, _I32, _P]),
+    "flic_create_ex": (_I32, [_I32, _I32, _P, _F64, _F32, _I32, _U32, _P]),
+    "flic_destroy": (_I32, [_P]),
+    "flic_get_tables": (_I32, [_P, _P, _P]),
+    "flic_edges": (_I32, [_P, _P, _P, _P]),
+    "flic_label": (_I32, [_P, _P, _P, _P]),
+    "flic_project": (_I32, [_P, _P, _I64, _P, _P, _P]),
+    "flic_range_buffer": (_P, [_P]),
+    "flic_scatter": (_I32, [_P, _P, _P, _I64, _P, _P]),
+    "flic_batch_create": (_I32, [_I32, _P]),
+    "flic_label_batch": (_I32, [_P, _P, _P, _P, _I32, _P]),
+    "flic_batch_destroy": (_I32, [_P]),
+    "flic_set_tuning": (_I32, [_P, _I32, _I32, _I32]),
+    "flic_batch_set_tuning": (_I32, [_P, _I32, _I32, _I32, _I32]),
+    "flic_plan_info": (_I32, [_P, _P]),
+    "flic_plan_frame": (_I32, [_I32, _I32, _I32, _I32, _I32, _P]),
+    "flic_batch_last_plan": (_I32, [_P, _P]),
+    "flic_device_status": (_I32, [_P, _I32]),
+    "flic_debug_set_iter_limit": (_I32, [_P, _I32]),
+}
+
+
+def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
+    if not os.path.exists(path):
+        raise RuntimeError(f"libflic.so not built at {path}; run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = load_library()
+
+
+class FlicError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"libflic status {status}: {message}")
+        self.status = status
+
+
+def _check(st: int) -> None:
+    if st != FLIC_OK:
+        raise FlicError(st, (_lib.flic_last_error() or b"").decode())
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _dptr(t, dtype_name: str, numel: int | None = None, what: str = "tensor") -> int:
+    """Device pointer of a contiguous CUDA tensor of the given dtype (and size)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise ValueError(f"{what} must be {dtype_name}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what} must have {numel} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+class Handle:
+    """A flic_handle plus the shape it was created with (closing is explicit or at GC)."""
+
+    def __init__(self, ptr: int, rows: int, cols: int, skip: int, delta: float, wrap: bool):
+        self.ptr = ptr
+        self.rows, self.cols, self.skip, self.delta, self.wrap = rows, cols, skip, delta, wrap
+
+    @property
+    def npix(self) -> int:
+        return self.rows * self.cols
+
+    def close(self) -> None:
+        if self.ptr:
+            _check(_lib.flic_destroy(self.ptr))
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                _lib.flic_destroy(self.ptr)
+        except Exception:
+            pass
+
+
+def flic_abi_version() -> int:
+    return _lib.flic_abi_version()
+
+
+def flic_create(rows: int, cols: int, elevation, az_step: float, delta: float, skip: int,
+                wrap: bool = True) -> Handle:
+    elev = np.ascontiguousarray(elevation, dtype=np.float64)
+    if elev.shape != (rows,):
+        raise ValueError("elevation must have one entry per row")
+    out = ctypes.c_void_p()
+    flags = 0 if wrap else FLIC_FLAG_NO_WRAP
+    _check(_lib.flic_create_ex(rows, cols, elev.ctypes.data, float(az_step), float(delta), skip,
+                               flags, ctypes.byref(out)))
+    return Handle(out.value, rows, cols, skip, float(np.float32(delta)), wrap)
+
+
+def flic_destroy(h: Handle) -> None:
+    h.close()
+
+
+def flic_get_tables(h: Handle):
+    kv = np.zeros((h.rows, h.skip), np.float32)
+    kh = np.zeros((h.rows, h.skip), np.float32)
+    _check(_lib.flic_get_tables(h.ptr, kv.ctypes.data, kh.ctypes.data))
+    return kv, kh
+
+
+def flic_plan_info(h: Handle) -> dict:
+    info = np.zeros(5, np.int32)
+    _check(_lib.flic_plan_info(h.ptr, info.ctypes.data))
+    return dict(strips=int(info[0]), strip_w=int(info[1]), pitch=int(info[2]),
+                smem=int(info[3]), threads=int(info[4]))
+
+
+def flic_plan_frame(rows: int, cols: int, skip: int, px_per_cta: int = 16384,
+                    max_cluster: int = 16) -> dict:
+    """Host-only strip split (no GPU needed)."""
+    info = np.zeros(4, np.int32)
+    _check(_lib.flic_plan_frame(rows, cols, skip, px_per_cta, max_cluster, info.ctypes.data))
+    return dict(strips=int(info[0]), strip_w=int(info[1]), pitch=int(info[2]), smem=int(info[3]))
+
+
+def flic_set_tuning(h: Handle, px_per_cta: int = 0, threads: int = 0, cluster: int = 0) -> None:
+    _check(_lib.flic_set_tuning(h.ptr, px_per_cta, threads, cluster))
+
+
+def flic_edges(h: Handle, range_img, mask, stream=None) -> None:
+    _check(_lib.flic_edges(h.ptr, _dptr(range_img, "float32", h.npix, "range"),
+                           _dptr(mask, "int16", h.npix, "mask"), _stream(stream)))
+
+
+def flic_label(h: Handle, range_img, labels, stream=None) -> None:
+    _check(_lib.flic_label(h.ptr, _dptr(range_img, "float32", h.npix, "range"),
+                           _dptr(labels, "int32", h.npix, "labels"), _stream(stream)))
+
+
+def flic_project(h: Handle, xyz, range_out, point_pixel, stream=None) -> None:
+    n = 0 if isinstance(xyz, int) else xyz.numel() // 3
+    if not isinstance(xyz, int) and xyz.numel() != 3 * n:
+        raise ValueError("xyz must hold n*3 floats")
+    _check(_lib.flic_project(h.ptr, _dptr(xyz, "float32", None, "xyz"), n,
+                             _dptr(range_out, "float32", h.npix, "range_out"),
+                             _dptr(point_pixel, "int32", n, "point_pixel"), _stream(stream)))
+
+
+def flic_range_buffer(h: Handle) -> int:
+    return _lib.flic_range_buffer(h.ptr)
+
+
+def flic_scatter(h: Handle, labels, point_pixel, point_labels, stream=None) -> None:
+    n = point_pixel.numel()
+    _check(_lib.flic_scatter(h.ptr, _dptr(labels, "int32", h.npix, "labels"),
+                             _dptr(point_pixel, "int32", n, "point_pixel"), n,
+                             _dptr(point_labels, "int32", n, "point_labels"), _stream(stream)))
+
+
+class Batch:
+    def __init__(self, ptr: int, max_frames: int):
+        self.ptr = ptr
+        self.max_frames = max_frames
+
+    def close(self) -> None:
+        if self.ptr:
+            _check(_lib.flic_batch_destroy(self.ptr))
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                _lib.flic_batch_destroy(self.ptr)
+        except Exception:
+            pass
+
+
+def flic_batch_create(max_frames: int) -> Batch:
+    out = ctypes.c_void_p()
+    _check(_lib.flic_batch_create(max_frames, ctypes.byref(out)))
+    return Batch(out.value, max_frames)
+
+
+def flic_batch_destroy(b: Batch) -> None:
+    b.close()
+
+
+def flic_batch_set_tuning(b: Batch, px_per_cta: int = 0, threads: int = 0, cluster: int = 0,
+                          ctas_per_sm: int = 0) -> None:
+    _check(_lib.flic_batch_set_tuning(b.ptr, px_per_cta, threads, cluster, ctas_per_sm))
+
+
+def flic_batch_last_plan(b: Batch) -> dict:
+    info = np.zeros(8, np.int32)
+    _check(_lib.flic_batch_last_plan(b.ptr, info.ctypes.data))
+    return dict(items=int(info[0]), grid_clusters=int(info[1]), cluster=int(info[2]),
+                threads=int(info[3]), smem=int(info[4]), strips=int(info[5]),
+                frames=int(info[6]))
+
+
+class BatchArgs:
+    """Host pointer arrays for flic_label_batch, built once and reused across calls."""
+
+    def __init__(self, handles, ranges, labels):
+        n = len(handles)
+        if not (len(ranges) == len(labels) == n):
+            raise ValueError("handles, ranges and labels must have the same length")
+        self.n = n
+        self.hs = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
+        self.rs = (ctypes.c_void_p * n)(*[_dptr(r, "float32", h.npix, "range")
+                                          for r, h in zip(ranges, handles)])
+        self.ls = (ctypes.c_void_p * n)(*[_dptr(l, "int32", h.npix, "labels")
+                                          for l, h in zip(labels, handles)])
+        self._keep = (handles, ranges, labels)
+
+
+def flic_label_batch(b: Batch, args: BatchArgs, stream=None) -> None:
+    _check(_lib.flic_label_batch(b.ptr, args.hs, args.rs, args.ls, args.n, _stream(stream)))
+
+
+def flic_device_status(h: Handle, clear: bool = True) -> int:
+    """FLIC_OK, or FLIC_ERR_TIMEOUT when a bounded device loop gave up."""
+    st = _lib.flic_device_status(h.ptr, 1 if clear else 0)
+    if st not in (FLIC_OK, FLIC_ERR_TIMEOUT):
+        _check(st)
+    return st
+
+
+def flic_debug_set_iter_limit(h: Handle, limit: int) -> None:
+    _check(_lib.flic_debug_set_iter_limit(h.ptr, limit))

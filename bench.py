@@ -1,0 +1,452 @@
+#!/usr/bin/env python
+"""Benchmark of the FLIC hot path (arXiv 2003.00575) on GB300.
+
+Workload (the batched configuration the throughput metric is quoted on): 256 synthetic
+frames of uneven shape drawn from {16x1800, 32x1024, 64x2048, 128x2048}, each with its
+own elevation table, delta in 0.3-0.6 m and skip S in 1..5, labelled by one persistent
+kernel launch replayed from a CUDA graph.  One step = one pass of the labelling path
+(neighbour test + union-find CCL + flatten) over the whole batch.
+
+Reported (one JSON line on rank 0):
+  value        batched labelled Mpixel/s over all ranks, inputs resident in HBM
+  e2e          the same through the public API with pinned host buffers: per step one
+               H2D copy of all range images and one D2H copy of all labels
+  per_frame    the same 256 frames as 256 flic_label launches (frames/s, Mpixel/s,
+               p50/p99 latency of one launch) and the batched/per-frame ratio
+  roofline     flic_label_kernel: algorithmic bytes (4 B range in + 4 B label out per
+               pixel) / mean launch time vs the measured HBM copy bandwidth
+  projection   flic_project + flic_label + flic_scatter on the 128x2048 occlusion frame
+               with 262,144 xyz points
+  cpu_baseline the CPU oracle (sequential BFS, 1 thread) on all 256 frames once
+L2 policy: three copies of the batch's buffers (~700 MB, > 129 MB L2) are used in
+rotation, so no step finds its inputs in L2.
+
+--impl reference times the CPU oracle (the plain sequential labeller) instead: one frame of
+the same batch per step, cycling, on the host cores of rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "labelled Mpixel/s & frames/s, batched vs per-frame; p50/p99 frame latency"
+UNIT = "Mpixel/s"
+WORKLOAD = ("c4 batch: 256 frames of uneven shape {16x1800, 32x1024, 64x2048, 128x2048}, "
+            "per-frame elevation table, delta U(0.3,0.6) m, skip U{1..5}, c2-style scenes; "
+            "one persistent launch under a CUDA graph")
+BYTES_PER_PX = 8  # 4 B range read + 4 B label written
+NCOPIES = 3
+PROFILE_NOTE = os.path.join(ROOT, "profiles", "flic_label_kernel.c4_batch.md")
+CSRC = os.path.join(ROOT, "paper_2003_00575_gb300", "csrc")
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["flic", "reference"], default="flic")
+    p.add_argument("--frames", type=int, default=256)
+    p.add_argument("--per-frame-reps", type=int, default=20)
+    p.add_argument("--e2e-steps", type=int, default=100)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--tuning", type=str, default="",
+                   help="px_per_cta,threads,cluster,ctas_per_sm for the batch (default: built-in)")
+    return p.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def source_sha() -> str:
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(CSRC)):
+        if fn.endswith((".cu", ".cuh", ".h")):
+            h.update(fn.encode())
+            h.update(open(os.path.join(CSRC, fn), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """DRAM bytes per launch from the committed ncu summary, if taken on these sources."""
+    if not os.path.exists(PROFILE_NOTE):
+        return None
+    text = open(PROFILE_NOTE).read()
+    sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
+    tr = re.search(r"traffic_bytes_per_launch_full_batch:\s*([0-9.eE+]+)", text)
+    if not sha or not tr or sha.group(1) != source_sha():
+        return None
+    return float(tr.group(1))
+
+
+def load_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = bus_id
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "100"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except OSError:
+            self.proc = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        time.sleep(0.15)
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[4]),
+                             [n for n, v in zip(self.NAMES, parts[5:9]) if v == "Active"]))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        loaded = [r for r in rows if r[2] >= 30] or rows
+        reasons = sorted({n for r in loaded for n in r[3]})
+        return {"sm_mhz": statistics.median(r[0] for r in loaded),
+                "sm_max_mhz": max(r[1] for r in rows), "reasons": reasons,
+                "samples": len(loaded)}
+
+
+def pct(xs, q):
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q))
+
+
+# ------------------------------------------------------------------------ reference arm
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    import oracle
+    from paper_2003_00575_gb300 import synth
+    frames = synth.config_c4(args.frames)
+    oracle.build()
+    times = []
+    px = 0
+    for i in range(args.warmup + args.steps):
+        f = frames[i % len(frames)]
+        t0 = time.perf_counter()
+        oracle.label(f.range, f.sensor.elevation, f.sensor.az_step, f.delta, f.skip)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(dt)
+            px += f.range.size
+    total = sum(times)
+    value = px / total / 1e6
+    sample = (f"one c4 frame per step, cycling through the {len(frames)} frames "
+              f"({args.steps} steps, {px} px), sequential C BFS labeller")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * total / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames": len(frames), "impl_note": "CPU oracle"},
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "frames_per_s": round(args.steps / total, 2),
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------------ flic arm
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+
+    import torch
+    from paper_2003_00575_gb300 import flic, synth
+
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- inputs: each rank labels its own 256 frames (weak scaling, no data collective)
+    frames = synth.config_c4(args.frames, first_seed=100 + rank * args.frames)
+    sizes = [f.range.size for f in frames]
+    offs = np.concatenate([[0], np.cumsum(sizes)])
+    total_px = int(offs[-1])
+    handles = [flic.flic_create(f.sensor.rows, f.sensor.cols, f.sensor.elevation,
+                                f.sensor.az_step, f.delta, f.skip) for f in frames]
+    host_range = torch.from_numpy(np.concatenate([f.range.reshape(-1) for f in frames]))
+    rng_dev = torch.empty((NCOPIES, total_px), dtype=torch.float32, device=dev)
+    lab_dev = torch.empty((NCOPIES, total_px), dtype=torch.int32, device=dev)
+    for k in range(NCOPIES):
+        rng_dev[k].copy_(host_range)
+    tun = [int(x) for x in args.tuning.split(",")] if args.tuning else None
+    batches, bargs = [], []
+    for k in range(NCOPIES):
+        b = flic.flic_batch_create(len(frames))
+        if tun:
+            flic.flic_batch_set_tuning(b, *tun)
+        batches.append(b)
+        bargs.append(flic.BatchArgs(
+            handles, [rng_dev[k, offs[i]:offs[i + 1]] for i in range(len(frames))],
+            [lab_dev[k, offs[i]:offs[i + 1]] for i in range(len(frames))]))
+    stream = torch.cuda.current_stream()
+
+    # ---- warm-up
+    for i in range(max(3, args.warmup)):
+        flic.flic_label_batch(batches[i % NCOPIES], bargs[i % NCOPIES], stream)
+    barrier()
+    plan = flic.flic_batch_last_plan(batches[0])
+
+    # ---- timed: K steps, events on the launching stream, clocks sampled meanwhile
+    bus = None
+    try:
+        props = torch.cuda.get_device_properties(dev)
+        bus = f"{props.pci_domain_id:08x}:{props.pci_bus_id:02x}:{props.pci_device_id:02x}.0"
+    except Exception:
+        bus = None
+    sampler = ClockSampler(bus)
+    sampler.start()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    t_wall0 = time.perf_counter()
+    evs[0].record(stream)
+    for i in range(args.steps):
+        flic.flic_label_batch(batches[i % NCOPIES], bargs[i % NCOPIES], stream)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    t_wall1 = time.perf_counter()
+    clocks = sampler.stop()
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[args.steps])
+    if dist is not None:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    value = total_px * world / (ms_per_step / 1e3) / 1e6
+    frames_per_s = len(frames) * world / (ms_per_step / 1e3)
+
+    # check the last outputs once (cheap invariant: every label is -1 or a valid index
+    # whose own label is itself); parity proper lives in tests/
+    lab0 = lab_dev[(args.steps - 1) % NCOPIES]
+    sane = True
+    for i in (0, len(frames) // 2, len(frames) - 1):
+        l = lab0[offs[i]:offs[i + 1]].long()
+        v = l[l >= 0]
+        sane &= bool(((v >= 0) & (v < sizes[i])).all().item())
+        if v.numel():
+            sane &= bool((l[v] == v).all().item())
+
+    # ---- roofline of flic_label_kernel (the only kernel in a step)
+    peak, peak_kind = load_peak()
+    mean_launch_s = statistics.mean(step_ms) / 1e3
+    achieved = BYTES_PER_PX * total_px / mean_launch_s / 1e9
+    traffic = committed_traffic()
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "traffic": traffic,
+                "peak_source": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
+                "kernel": "flic_label_kernel",
+                "algorithmic_bytes_per_launch": BYTES_PER_PX * total_px}
+
+    # ---- per-frame launches: the same frames, one flic_label call each
+    single_lat = []
+    pf_total = []
+    pf_evs = [torch.cuda.Event(enable_timing=True) for _ in range(len(frames) + 1)]
+    for rep in range(args.per_frame_reps + 2):
+        k = rep % NCOPIES
+        pf_evs[0].record(stream)
+        for i, h in enumerate(handles):
+            flic.flic_label(h, rng_dev[k, offs[i]:offs[i + 1]], lab_dev[k, offs[i]:offs[i + 1]],
+                            stream)
+            pf_evs[i + 1].record(stream)
+        torch.cuda.synchronize()
+        if rep >= 2:
+            pf_total.append(pf_evs[0].elapsed_time(pf_evs[-1]))
+            single_lat += [pf_evs[i].elapsed_time(pf_evs[i + 1]) for i in range(len(frames))]
+    pf_ms = statistics.mean(pf_total)
+    per_frame = {
+        "frames_per_s": round(len(frames) / (pf_ms / 1e3), 1),
+        "mpixel_per_s": round(total_px / (pf_ms / 1e3) / 1e6, 1),
+        "ms_per_256_frames": round(pf_ms, 4),
+        "latency_ms_p50": round(pct(single_lat, 50), 4),
+        "latency_ms_p99": round(pct(single_lat, 99), 4),
+    }
+
+    # ---- e2e: public API with pinned host buffers, copies inside the timed region
+    host_in = host_range.pin_memory()
+    host_out = torch.empty(total_px, dtype=torch.int32).pin_memory()
+    e2e_steps = max(3, args.e2e_steps)
+    for i in range(3):
+        rng_dev[0].copy_(host_in, non_blocking=True)
+        flic.flic_label_batch(batches[0], bargs[0], stream)
+        host_out.copy_(lab_dev[0], non_blocking=True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    e0.record(stream)
+    for i in range(e2e_steps):
+        rng_dev[0].copy_(host_in, non_blocking=True)
+        flic.flic_label_batch(batches[0], bargs[0], stream)
+        host_out.copy_(lab_dev[0], non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / e2e_steps
+    if dist is not None:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = {"value": round(total_px * world / (e2e_ms / 1e3) / 1e6, 1), "unit": UNIT,
+           "h2d_bytes_per_step": 4 * total_px, "d2h_bytes_per_step": 4 * total_px,
+           "ms_per_step": round(e2e_ms, 4)}
+
+    # ---- projection path on the occlusion-heavy 128x2048 frame (262,144 points)
+    f3 = synth.config_c3()
+    s3 = f3.sensor
+    h3 = flic.flic_create(s3.rows, s3.cols, s3.elevation, s3.az_step, f3.delta, f3.skip)
+    xyz = torch.from_numpy(f3.xyz).to(dev)
+    rimg = torch.empty(s3.rows * s3.cols, dtype=torch.float32, device=dev)
+    pix = torch.empty(f3.xyz.shape[0], dtype=torch.int32, device=dev)
+    lab3 = torch.empty(s3.rows * s3.cols, dtype=torch.int32, device=dev)
+    plab = torch.empty_like(pix)
+    pe = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    lat_proj = []
+    for rep in range(53):
+        pe[0].record(stream)
+        flic.flic_project(h3, xyz, rimg, pix, stream)
+        pe[1].record(stream)
+        flic.flic_label(h3, rimg, lab3, stream)
+        pe[2].record(stream)
+        flic.flic_scatter(h3, lab3, pix, plab, stream)
+        pe[3].record(stream)
+        torch.cuda.synchronize()
+        if rep >= 3:
+            lat_proj.append([pe[0].elapsed_time(pe[1]), pe[1].elapsed_time(pe[2]),
+                             pe[2].elapsed_time(pe[3]), pe[0].elapsed_time(pe[3])])
+    lp = np.array(lat_proj)
+    projection = {
+        "workload": "c3 128x2048 S5 delta 0.4, 262,144 xyz points",
+        "ms_project": round(float(np.median(lp[:, 0])), 4),
+        "ms_label": round(float(np.median(lp[:, 1])), 4),
+        "ms_scatter": round(float(np.median(lp[:, 2])), 4),
+        "latency_ms_p50": round(pct(lp[:, 3], 50), 4),
+        "latency_ms_p99": round(pct(lp[:, 3], 99), 4),
+        "mpoints_per_s": round(f3.xyz.shape[0] / (float(np.median(lp[:, 3])) / 1e3) / 1e6, 1),
+    }
+    h3.close()
+
+    # ---- CPU baseline: the oracle as it stands, 1 thread, all frames once (rank 0, N=1)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle  # CPU baseline leg only
+        oracle.build()
+        t0 = time.perf_counter()
+        for f in frames:
+            oracle.label(f.range, f.sensor.elevation, f.sensor.az_step, f.delta, f.skip)
+        dt = time.perf_counter() - t0
+        cpu = {"value": round(total_px / dt / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"all {len(frames)} c4 frames once ({total_px} px, {dt:.2f} s), "
+                         f"sequential C BFS labeller, 1 thread of {os.cpu_count()} host cores",
+               "frames_per_s": round(len(frames) / dt, 2)}
+
+    for h in handles:
+        st = flic.flic_device_status(h)
+        sane &= st == flic.FLIC_OK
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_gpu": len(frames),
+                       "pixels_per_gpu": total_px,
+                       "l2": f"inputs larger than L2: {NCOPIES} buffer copies in rotation "
+                             f"({NCOPIES * 8 * total_px / 1e6:.0f} MB)",
+                       "parallelism": f"frames sharded, {world} rank(s)",
+                       "launch": plan},
+            "frames_per_s": round(frames_per_s, 1),
+            "latency_ms_p50": round(pct(step_ms, 50), 4),
+            "latency_ms_p99": round(pct(step_ms, 99), 4),
+            "per_frame": per_frame,
+            "batched_vs_per_frame": round(frames_per_s / world / per_frame["frames_per_s"], 2),
+            "e2e": e2e,
+            "roofline": roofline,
+            "projection": projection,
+            "cpu_baseline": cpu,
+            "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "clock_samples": clocks["samples"],
+            "gpu_launches": args.steps,
+            "wall_s_timed": round(t_wall1 - t_wall0, 3),
+            "outputs_sane": bool(sane),
+            "paper_context": "paper: up to 165 Hz, Python, one i7-6820HQ core (not comparable)",
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

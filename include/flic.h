@@ -71,7 +71,7 @@ typedef enum {
  * A frame is split into at most 16 full-height column strips of at most 32768 (padded)
  * pixels each; a shape that does not fit gives FLIC_ERR_UNSUPPORTED from flic_create. */
 #define FLIC_MAX_PIXELS (1 << 19)
-#define FLIC_MAX_ROWS 1024
+#define FLIC_MAX_ROWS 512
 #define FLIC_MAX_SKIP 8
 
 /* ABI version compiled into the library (FLIC_ABI_VERSION of its build). */
@@ -180,9 +180,10 @@ flic_status flic_scatter(flic_handle h, const int32_t* labels, const int32_t* po
  *             shape, tables, delta and skip)
  *   ranges    host array of nframes device pointers (frame i: rows_i*cols_i fp32)
  *   labels    host array of nframes device pointers (frame i: rows_i*cols_i int32)
- *   The host arrays are read during the call only.  Calls on one batch object are
- *   serialised on their streams by the object (a call waits until the previous call's
- *   descriptor upload has finished before rewriting its staging buffer).
+ *   The host arrays are read during the call only.  A call with the same handles and
+ *   buffers as the previous call on this object only replays the captured launch; any
+ *   other call re-plans, waits on the host until the previous descriptor upload has left
+ *   the staging buffer, and orders its upload after the previous launch on the device.
  *   Errors: INVALID, BUSY (nframes > max_frames), CUDA.
  * flic_batch_destroy — frees the object.  Synchronises.  NULL is accepted.
  */

@@ -47,13 +47,22 @@ struct LabelLaunch {
     FrameDesc single;
 };
 
-// Shared memory (bytes) one block needs for a strip of `rows` x `width` columns.
-inline size_t strip_smem_bytes(int rows, int pitch_log2) {
+// Shared memory (bytes) one block needs for a strip of `rows` x `width` columns with
+// local pitch 1 << pitch_log2 and skip S: the staged readings (rows x (width + S) rounded
+// up to 4, later reused as the parent array, rows x pitch ints), the 16-bit edge masks
+// (rows x pitch) and two sets of ballot words (rows x pitch / 32 each).
+inline size_t strip_smem_bytes(int rows, int pitch_log2, int width, int skip) {
     size_t pitch = size_t(1) << pitch_log2;
-    size_t par = size_t(rows) * pitch * 4;
-    size_t hmask = size_t(rows) * (pitch / 32) * 4;
-    return par + hmask + 64;
+    size_t rp = (size_t(width) + size_t(skip) + 3) & ~size_t(3);
+    size_t a = size_t(rows) * (rp > pitch ? rp : pitch) * 4;
+    size_t mask = size_t(rows) * pitch * 2;
+    size_t words = size_t(rows) * (pitch / 32) * 4;  // run ballots + validity ballots
+    return a + mask + 2 * words + 64;
 }
+
+// Dynamic shared memory one block may use (227 KB opt-in on sm_100/sm_103, minus the
+// kernel's static shared memory).
+constexpr size_t kMaxDynSmem = 227 * 1024 - 256;
 
 // Kernel launchers (flic_label.cu / flic_project.cu).  Return cudaGetLastError().
 cudaError_t launch_label(const LabelLaunch& L, int grid_clusters, int threads, size_t smem,

@@ -4,25 +4,34 @@
 // strips of one or more frames.  Each block owns one strip (rows x W columns) and runs:
 //
 //   phase 1  (edge test + tile-local union, in shared memory)
-//            a. each warp takes a 32-column row segment; the horizontal offset-1 edge
-//               bits (Eq. 2/3) of the segment are gathered with __ballot_sync and every
-//               pixel's parent is set to the first pixel of its run, so a run of joined
-//               pixels becomes one star without a single atomic;
-//            b. the remaining edges — offset-1 links across segment borders, offsets
-//               2..S along the row (Map Connections, §III-B-2) and offsets 1..S down the
-//               column — are tested; an edge whose two ends are already joined by runs
-//               is dropped with ballot bit tricks, lanes asking for the same union are
-//               merged with __match_any_sync, and the rest hook with shared-memory
-//               atomicMin (the smaller index becomes the root);
-//            c. paths are compressed, so every pixel points at its strip-local root,
-//               the minimum index of its strip-local component;
+//            0. the strip's range readings, plus S halo columns on the right (wrapping to
+//               column 0 at the seam), are staged into shared memory: one TMA bulk copy
+//               (cp.async.bulk) per row completing on an mbarrier, or plain loads when the
+//               frame is not 16-byte aligned;
+//            1. every pixel's 2S edge bits (Eq. 2/3; offsets 1..S right and down, the
+//               Map Connections of §III-B-2) are computed from shared memory into a 16-bit
+//               mask per pixel; the staged readings are dead afterwards and their space
+//               becomes the parent array;
+//            a. each warp takes a 32-column row segment; the offset-1 right bits of the
+//               segment are gathered with __ballot_sync and every pixel's parent is set to
+//               the first pixel of its run, so a run of joined pixels becomes one star
+//               without a single atomic;
+//            b. the remaining in-strip edges — offset-1 links across segment borders,
+//               offsets 2..S along the row and 1..S down the column — are read from the
+//               masks; an edge whose two ends are already joined by runs is dropped with
+//               ballot bit tricks, lanes asking for the same union are merged with
+//               __match_any_sync, and the rest hook with shared-memory atomicMin (the
+//               smaller index becomes the root);
+//            c. paths are compressed by pointer jumping, so every pixel points at its
+//               strip-local root, the minimum index of its strip-local component;
 //            d. pixels in the first S columns publish their root in the frame's labels
 //               buffer, and roots of components touching either strip border publish
 //               themselves: these entries form the cross-strip forest.
 //   cluster barrier
 //   phase 2  (boundary merge, global memory): every edge that leaves the strip on the
-//            right (offsets 1..S, including the azimuth wrap from the last column to the
-//            first) unites the two roots with atomicMin hooking and path halving.
+//            right (mask bits of offsets 1..S, including the azimuth wrap from the last
+//            column to the first) unites the two roots with atomicMin hooking and path
+//            halving.
 //   cluster barrier
 //   phase 3  (flatten): roots of border components look up their global root (read-only);
 //            every pixel then writes label = the minimum linear index of its component,
@@ -55,119 +64,336 @@ struct Strip {
     bool border;   // edges can leave the strip (several strips or wrap-around)
     int c0, W;     // first column and width of the strip
     int sh;        // local pitch = 1 << sh (>= 32, >= W)
+    int RP;        // row pitch of the staged readings (>= W + S, multiple of 4)
+    bool bulk;     // rows are 16-byte aligned: stage with TMA bulk copies
     int limit;
 };
+
+// Shared-memory carve-up of one strip (byte offsets; see strip_smem_bytes on the host).
+struct Carve {
+    float* stage;       // R x RP staged readings; reused as the parent array (R x P)
+    int* par;
+    uint16_t* mask;     // R x P edge bits
+    unsigned* hmask;    // R x P/32 ballot words of the offset-1 right bits
+    unsigned* vmask;    // R x P/32 ballot words: the pixel is a measurement
+};
+
+__device__ __forceinline__ Carve carve(unsigned char* base, const Strip& s) {
+    Carve c;
+    const int P = 1 << s.sh;
+    const int a_words = s.R * (s.RP > P ? s.RP : P);
+    c.stage = reinterpret_cast<float*>(base);
+    c.par = reinterpret_cast<int*>(base);
+    c.mask = reinterpret_cast<uint16_t*>(base + 4 * (size_t)a_words);
+    c.hmask = reinterpret_cast<unsigned*>(base + 4 * (size_t)a_words + 2 * (size_t)s.R * P);
+    c.vmask = c.hmask + (s.R << (s.sh - 5));
+    return c;
+}
 
 __device__ __forceinline__ int global_of(const Strip& s, int local) {
     return (local >> s.sh) * s.C + s.c0 + (local & ((1 << s.sh) - 1));
 }
 
-// Union two pixels of the strip unless another lane of the warp asks for the same union
-// (same current parents of both ends).  All 32 lanes of the warp must call it.
-__device__ __forceinline__ void warp_union(int* par, bool need, int i, int j, int lane,
-                                           const Strip& s) {
-    unsigned nm = __ballot_sync(kFull, need);
-    if (nm == 0) return;
-    if (__popc(nm) > 1) {
-        // parents < 2^15, so a real key never equals the idle-lane key
-        unsigned key = need ? ((unsigned(par[i]) << 16) | unsigned(par[j])) : kFull;
-        unsigned grp = __match_any_sync(kFull, key);
-        if (need && (__ffs(grp) - 1) != lane) need = false;
-    }
-    if (need) {
-        int budget = s.limit;
-        union_smem(par, i, j, budget);
-        if (budget <= 0) report_timeout(s.status);
-    }
+// Union of two pixels of the strip (the caller has already dropped redundant requests).
+__device__ __forceinline__ void unite(int* par, int a, int b, const Strip& s) {
+    int budget = s.limit;
+    union_smem(par, a, b, budget);
+    if (budget <= 0) report_timeout(s.status);
 }
 
-__device__ void phase1_local(const Strip& s, int* par, unsigned* hmask) {
+// b. every edge inside the strip that the runs do not already cover.  Each warp walks a
+//    band of consecutive rows of one 32-column segment from the top down and keeps, in
+//    registers, the labels and edge masks of the S rows above each of its columns.  A
+//    run whose vertical edges all reach pixels of one label X (the common case: ground,
+//    walls) just hooks its first pixel under X with one atomicMin; only where several
+//    labels meet are real unions needed, one per distinct (run, label) pair, found with
+//    __match_any_sync.  Edges that leave the band or the segment use plain unions, with
+//    the requests a neighbouring lane already covers dropped by ballot bit tricks.
+template <int S>
+__device__ void phase1_bands(const Strip& s, const Carve& sm) {
+    constexpr int kInf = 0x7fffffff;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int P = 1 << s.sh;
+    const int segs_log2 = s.sh - 5;
+    const int nseg = 1 << segs_log2;
+    int* par = sm.par;
+    const int band = (s.R * nseg + nwarps - 1) / nwarps;  // rows per band
+    const int nbands = (s.R + band - 1) / band;
+    const unsigned lane_lt = (1u << lane) - 1u;
+
+    for (int blk = warp; blk < nbands * nseg; blk += nwarps) {
+        const int seg = blk & (nseg - 1);
+        const int r0 = (blk >> segs_log2) * band;
+        const int r1 = min(s.R, r0 + band);
+        const int c = (seg << 5) + lane;
+        const bool inw = c < s.W;
+        int lab[S];        // lab[k-1]: a label (set member) of pixel (r-k, c), -1 if none
+        unsigned mab[S];   // mab[k-1]: edge mask of pixel (r-k, c)
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            lab[k] = -1;
+            mab[k] = 0u;
+        }
+        for (int r = r0; r < r1; ++r) {
+            const int u = (r << segs_log2) + seg;
+            const int base = (r << s.sh) + (seg << 5);
+            const int i = base + lane;
+            const unsigned mk = inw ? sm.mask[i] : 0u;
+            const unsigned m = sm.hmask[u];
+            const bool va = inw && ((sm.vmask[u] >> lane) & 1u);
+            // this lane's run: first lane st, last lane en, lanes runbits
+            const unsigned below = ~m & lane_lt;
+            const int st = below ? 32 - __clz(below) : 0;
+            const unsigned brk = (~m | 0x80000000u) & ~lane_lt;
+            const int en = __ffs(brk) - 1;
+            const unsigned runbits = (en == 31 ? kFull : ((2u << en) - 1u)) & ~((1u << st) - 1u);
+            const int sidx = base + st;
+
+            // labels of the pixels above that a vertical edge joins to this pixel: the
+            // smallest in cand, and whether they differ
+            int cand = kInf;
+            bool multi = false;
+#pragma unroll
+            for (int k = 1; k <= S; ++k) {
+                if (r - k < 0) break;
+                if (r - k >= r0) {
+                    if ((mab[k - 1] >> (8 + k - 1)) & 1u) {
+                        const int L = lab[k - 1];
+                        multi |= cand != kInf && L != cand;
+                        cand = min(cand, L);
+                    }
+                } else {
+                    // from a row of the band above: plain union, unless lane l-1 has the
+                    // same edge and both rows join l-1 to l
+                    const int ia = ((r - k) << s.sh) + c;
+                    const bool e = inw && ((sm.mask[ia] >> (8 + k - 1)) & 1u);
+                    const unsigned em = __ballot_sync(kFull, e);
+                    const unsigned mb = sm.hmask[((r - k) << segs_log2) + seg];
+                    const unsigned implied = (em & m & mb) << 1;
+                    if (e && !((implied >> lane) & 1u)) unite(par, ia, i, s);
+                }
+            }
+            const unsigned hasm = __ballot_sync(kFull, cand != kInf);
+            int mylab = va ? sidx : -1;
+            if (hasm) {
+                const int X = __shfl_sync(kFull, cand, __ffs(hasm) - 1);
+                const unsigned uni = __ballot_sync(kFull, !multi && (cand == kInf || cand == X));
+                if (uni == kFull) {
+                    if (va && (hasm & runbits)) {
+                        mylab = X;
+                        if (lane == st) {
+                            const int old = atomicMin(par + sidx, X);
+                            if (old != sidx && old != X) unite(par, old, X, s);
+                        } else {
+                            par[i] = X;  // shortcut for the compression pass
+                        }
+                    }
+                } else {
+                    // several labels meet: one union per distinct (run, label) pair and
+                    // offset
+#pragma unroll
+                    for (int k = 1; k <= S; ++k) {
+                        if (r - k < r0) break;
+                        const int ck = ((mab[k - 1] >> (8 + k - 1)) & 1u) ? lab[k - 1] : kInf;
+                        const unsigned key =
+                            ck == kInf ? kFull : ((unsigned)st << 16) | (unsigned)ck;
+                        const unsigned grp = __match_any_sync(kFull, key);
+                        if (ck != kInf && (__ffs(grp) - 1) == lane) unite(par, sidx, ck, s);
+                    }
+                    __syncwarp();
+                    int root = 0;
+                    if (va && lane == st) {
+                        int budget = s.limit;
+                        root = find_smem(par, sidx, budget);
+                    }
+                    root = __shfl_sync(kFull, root, st);
+                    if (va) {
+                        mylab = root;
+                        if (lane != st) par[i] = root;
+                    }
+                }
+            }
+
+            // offsets 2..S along the row
+#pragma unroll
+            for (int k = 2; k <= S; ++k) {
+                const int stp = __shfl_down_sync(kFull, st, k);  // run start of lane + k
+                const bool e = ((mk >> (k - 1)) & 1u) && c + k < s.W;
+                const bool inseg = lane + k <= 31;
+                const bool e_in = e && inseg && stp != st;
+                const unsigned eb = __ballot_sync(kFull, e_in);
+                if (e_in) {
+                    // implied by lane l-1 when l-1 ~ l and l-1+k ~ l+k by runs
+                    const bool imp = lane > 0 && ((eb >> (lane - 1)) & 1u) &&
+                                     ((m >> (lane - 1)) & 1u) && ((m >> (lane + k - 1)) & 1u);
+                    if (!imp) unite(par, sidx, base + stp, s);
+                } else if (e && !inseg) {
+                    // into the next segment: covered when this run reaches lane 31, joins
+                    // lane 0 of the next segment, and the target lies in that first run
+                    const int t = lane + k - 32;
+                    const unsigned mn = sm.hmask[u + 1];
+                    const unsigned need_bits = (1u << t) - 1u;
+                    const bool joined = en == 31 && ((m >> 31) & 1u) && ((mn & need_bits) == need_bits);
+                    if (!joined) unite(par, i, i + k, s);
+                }
+            }
+            // offset-1 link from lane 31 into the next segment (h1 implies c + 1 < W)
+            if (lane == 31 && ((m >> 31) & 1u)) unite(par, i, i + 1, s);
+
+#pragma unroll
+            for (int k = S - 1; k > 0; --k) {
+                lab[k] = lab[k - 1];
+                mab[k] = mab[k - 1];
+            }
+            lab[0] = mylab;
+            mab[0] = mk;
+        }
+    }
+}
+
+// Stage the strip and its halo into shared memory and compute the edge masks.
+__device__ void phase1_edges(const Strip& s, const Carve& sm, uint64_t* bar, uint32_t parity) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+
+    // 0. staging
+    if (s.bulk) {
+        if (warp == 0) {
+            // the previous item used this memory through ordinary loads and stores
+            fence_proxy_async_smem();
+            if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(s.R * s.W * 4));
+            __syncwarp();
+            for (int r = lane; r < s.R; r += 32)
+                bulk_copy_g2s(sm.stage + r * s.RP, s.range + (size_t)r * s.C + s.c0,
+                              (uint32_t)(s.W * 4), bar);
+        }
+    } else {
+        for (int r = warp; r < s.R; r += nwarps)
+            for (int c = lane; c < s.W; c += 32)
+                sm.stage[r * s.RP + c] = __ldg(s.range + (size_t)r * s.C + s.c0 + c);
+    }
+    // halo: S columns right of the strip (wrapping at the seam; 0 past the last column)
+    for (int t = threadIdx.x; t < s.R * s.S; t += blockDim.x) {
+        const int r = t / s.S;
+        const int j = t - r * s.S;
+        int col = s.c0 + s.W + j;
+        float v = 0.0f;
+        if (col >= s.C && s.wrap) col %= s.C;
+        if (col < s.C) v = __ldg(s.range + (size_t)r * s.C + col);
+        sm.stage[r * s.RP + s.W + j] = v;
+    }
+    if (s.bulk) {
+        if (!mbar_wait(bar, parity, 1 << 22)) {
+            report_timeout(s.status);
+            mbar_wait(bar, parity, 1 << 22);  // let the copies in flight land
+        }
+    }
+    __syncthreads();
+
+    // 1. edge bits of every pixel, from shared memory
+    for (int r = warp; r < s.R; r += nwarps) {
+        float kh[kMaxSkip], kv[kMaxSkip];
+#pragma unroll
+        for (int k = 0; k < kMaxSkip; ++k) {
+            kh[k] = k < s.S ? __ldg(s.kh + r * s.S + k) : 0.0f;
+            kv[k] = k < s.S ? __ldg(s.kv + r * s.S + k) : 0.0f;
+        }
+        const float* row = sm.stage + r * s.RP;
+        for (int cs = 0; cs < s.W; cs += 32) {  // same trip count on every lane
+            const int c = cs + lane;
+            const float a = c < s.W ? row[c] : 0.0f;
+            const bool va = valid_range(a);
+            unsigned m = 0;
+            if (va) {
+#pragma unroll
+                for (int k = 1; k <= kMaxSkip; ++k) {
+                    if (k > s.S) break;
+                    const float b = row[c + k];
+                    if (valid_range(b) && edge_pred(a, b, kh[k - 1], s.delta2)) m |= 1u << (k - 1);
+                    if (r + k < s.R) {
+                        const float d = row[c + k * s.RP];
+                        if (valid_range(d) && edge_pred(a, d, kv[k - 1], s.delta2))
+                            m |= 1u << (8 + k - 1);
+                    }
+                }
+            }
+            const unsigned vm = __ballot_sync(kFull, va);
+            if (c < s.W) sm.mask[(r << s.sh) + c] = (uint16_t)m;
+            if (lane == 0) sm.vmask[(r << (s.sh - 5)) + (cs >> 5)] = vm;
+        }
+    }
+    __syncthreads();
+}
+
+__device__ void phase1_local(const Strip& s, const Carve& sm) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
     const int segs_log2 = s.sh - 5;
     const int nunits = s.R << segs_log2;
+    int* par = sm.par;
+    unsigned* hmask = sm.hmask;
 
     // a. runs of horizontally joined pixels become stars
     for (int u = warp; u < nunits; u += nwarps) {
         const int r = u >> segs_log2;
         const int seg = u & ((1 << segs_log2) - 1);
         const int c = (seg << 5) + lane;
-        const float* rp = s.range + (size_t)r * s.C + s.c0;
-        const float a = c < s.W ? load_range(rp + c) : 0.0f;
-        const float b = c + 1 < s.W ? load_range(rp + c + 1) : 0.0f;
-        const bool h1 = a > 0.0f && b > 0.0f && edge_pred(a, b, __ldg(s.kh + r * s.S), s.delta2);
+        const unsigned mk = c < s.W ? sm.mask[(r << s.sh) + c] : 0u;
+        const bool h1 = (mk & 1u) && c + 1 < s.W;
         const unsigned m = __ballot_sync(kFull, h1);
         if (lane == 0) hmask[u] = m;
         // first lane of this lane's run: one past the highest missing link below it
         const unsigned below = ~m & ((1u << lane) - 1u);
         const int start = below ? 32 - __clz(below) : 0;
-        par[(r << s.sh) + c] = a > 0.0f ? (r << s.sh) + (seg << 5) + start : -1;
+        // (validity words of segments that lie wholly past the strip width are never
+        //  written; every lane there has c >= W)
+        const bool va = c < s.W && ((sm.vmask[u] >> lane) & 1u);
+        par[(r << s.sh) + c] = va ? (r << s.sh) + (seg << 5) + start : -1;
     }
     __syncthreads();
 
-    // b. every other edge inside the strip
-    for (int u = warp; u < nunits; u += nwarps) {
-        const int r = u >> segs_log2;
-        const int seg = u & ((1 << segs_log2) - 1);
-        const int c = (seg << 5) + lane;
-        const float* rp = s.range + (size_t)r * s.C + s.c0;
-        const float a = c < s.W ? load_range(rp + c) : 0.0f;
-        const bool va = a > 0.0f;
-        const unsigned m = hmask[u];
-        const int i = (r << s.sh) + c;
-
-        // offset-1 link from the last lane into the next segment (h1 implies c + 1 < W)
-        {
-            const bool need = lane == 31 && ((m >> 31) & 1u);
-            warp_union(par, need, i, i + 1, lane, s);
-        }
-        // offsets 2..S along the row
-        for (int k = 2; k <= s.S; ++k) {
-            bool e = false;
-            if (va && c + k < s.W) {
-                const float b = load_range(rp + c + k);
-                e = b > 0.0f && edge_pred(a, b, __ldg(s.kh + r * s.S + k - 1), s.delta2);
-            }
-            if (e && lane + k <= 31) {
-                const unsigned run = (m >> lane) & ((1u << k) - 1u);
-                if (run == (1u << k) - 1u) e = false;  // same run already
-            }
-            warp_union(par, e, i, i + k, lane, s);
-        }
-        // offsets 1..S down the column
-        for (int k = 1; k <= s.S && r + k < s.R; ++k) {
-            bool e = false;
-            if (va) {
-                const float b = load_range(rp + (size_t)k * s.C + c);
-                e = b > 0.0f && edge_pred(a, b, __ldg(s.kv + r * s.S + k - 1), s.delta2);
-            }
-            const unsigned em = __ballot_sync(kFull, e);
-            const unsigned mk = hmask[u + (k << segs_log2)];
-            // lane l is implied by lane l-1 when l-1 has the same vertical edge and both
-            // rows join l-1 to l by a horizontal offset-1 edge
-            const unsigned implied = (em & m & mk) << 1;
-            const bool need = e && !((implied >> lane) & 1u);
-            warp_union(par, need, i, i + (k << s.sh), lane, s);
-        }
+    switch (s.S) {
+        case 1: phase1_bands<1>(s, sm); break;
+        case 2: phase1_bands<2>(s, sm); break;
+        case 3: phase1_bands<3>(s, sm); break;
+        case 4: phase1_bands<4>(s, sm); break;
+        case 5: phase1_bands<5>(s, sm); break;
+        case 6: phase1_bands<6>(s, sm); break;
+        case 7: phase1_bands<7>(s, sm); break;
+        default: phase1_bands<8>(s, sm); break;
     }
     __syncthreads();
 
-    // c. compress: every measurement points at its strip-local root (read-only finds;
-    //    each thread stores only its own entries)
+    // c. compress by pointer jumping: every round replaces each parent by its parent's
+    //    parent; each entry has exactly one writer (its owner thread), so a round never
+    //    stores a stale value over a newer one, and ceil(log2(depth)) rounds reach the roots
     {
         volatile int* vp = par;
-        for (int i = threadIdx.x; i < (s.R << s.sh); i += blockDim.x) {
-            if (vp[i] >= 0) {
-                int budget = s.limit;
-                const int root = find_smem_ro(vp, i, budget);
-                if (budget <= 0) report_timeout(s.status);
-                vp[i] = root;
+        const int n = s.R << s.sh;
+        int rounds = 0;
+        bool changed = true;
+        while (changed) {
+            bool any = false;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int p = vp[i];
+                if (p >= 0) {
+                    const int gp = vp[p];
+                    if (gp != p) {
+                        vp[i] = gp;
+                        any = true;
+                    }
+                }
+            }
+            changed = __syncthreads_or(any) != 0;
+            if (++rounds > 40) {  // depth < 2^16: 17 rounds suffice
+                if (threadIdx.x == 0) report_timeout(s.status);
+                break;
             }
         }
     }
-    __syncthreads();
 
     // d. publish the border pixels and border roots into the cross-strip forest
     if (s.border) {
@@ -184,35 +410,27 @@ __device__ void phase1_local(const Strip& s, int* par, unsigned* hmask) {
             __stcg(s.labels + groot, groot);
         }
     }
-    (void)P;
 }
 
-__device__ void phase2_merge(const Strip& s, const int* par) {
+__device__ void phase2_merge(const Strip& s, const Carve& sm) {
     if (!s.border) return;
     const int first = s.W - s.S > 0 ? s.W - s.S : 0;
     const int ncols = s.W - first;
-    const int n = s.R * ncols * s.S;
+    const int n = s.R * ncols;
     for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int k = t % s.S + 1;
-        const int rc = t / s.S;
-        const int r = rc / ncols;
-        const int c = first + (rc - r * ncols);
-        if (c + k < s.W) continue;  // stays inside the strip: phase 1 handled it
-        int tc = s.c0 + c + k;
-        if (tc >= s.C) {
-            if (!s.wrap) continue;
-            tc %= s.C;
+        const int r = t / ncols;
+        const int c = first + (t - r * ncols);
+        const unsigned mk = sm.mask[(r << s.sh) + c];
+        for (int k = s.W - c; k <= s.S; ++k) {  // offsets that leave the strip
+            if (!((mk >> (k - 1)) & 1u)) continue;
+            int tc = s.c0 + c + k;
+            if (tc >= s.C) tc %= s.C;  // a set bit past the last column implies wrap
+            const int ga = global_of(s, sm.par[(r << s.sh) + c]);
+            const int gb = __ldcg(s.labels + (size_t)r * s.C + tc);
+            int budget = s.limit;
+            union_global(s.labels, ga, gb, budget);
+            if (budget <= 0) report_timeout(s.status);
         }
-        const float a = load_range(s.range + (size_t)r * s.C + s.c0 + c);
-        if (!(a > 0.0f)) continue;
-        const float b = load_range(s.range + (size_t)r * s.C + tc);
-        if (!(b > 0.0f)) continue;
-        if (!edge_pred(a, b, __ldg(s.kh + r * s.S + k - 1), s.delta2)) continue;
-        const int ga = global_of(s, par[(r << s.sh) + c]);
-        const int gb = __ldcg(s.labels + (size_t)r * s.C + tc);
-        int budget = s.limit;
-        union_global(s.labels, ga, gb, budget);
-        if (budget <= 0) report_timeout(s.status);
     }
 }
 
@@ -273,7 +491,10 @@ __device__ void phase3_flatten(const Strip& s, int* par) {
 
 __global__ void __launch_bounds__(1024) flic_label_kernel(const LabelLaunch L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    int* par = reinterpret_cast<int*>(smem_raw);
+    __shared__ __align__(8) uint64_t tma_bar;
+    if (threadIdx.x == 0) mbar_init(&tma_bar, 1);
+    __syncthreads();
+    uint32_t parity = 0;
 
     const unsigned rank = cluster_ctarank();
     const int nitems = L.items ? L.nitems : 1;
@@ -306,17 +527,24 @@ __global__ void __launch_bounds__(1024) flic_label_kernel(const LabelLaunch L) {
             s.c0 = si * f.strip_w;
             s.W = min(f.strip_w, s.C - s.c0);
             s.sh = f.pitch_log2;
+            s.RP = (s.W + s.S + 3) & ~3;
+            s.bulk = ((s.C & 3) == 0) && ((s.c0 & 3) == 0) && ((s.W & 3) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(s.range) & 15) == 0);
             s.limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
         }
-        unsigned* hmask = reinterpret_cast<unsigned*>(par + (active ? (s.R << s.sh) : 0));
+        const Carve sm = carve(smem_raw, s);
 
-        if (active) phase1_local(s, par, hmask);
+        if (active) {
+            phase1_edges(s, sm, &tma_bar, parity);
+            if (s.bulk) parity ^= 1u;
+            phase1_local(s, sm);
+        }
         __threadfence();
         cluster_barrier();
-        if (active) phase2_merge(s, par);
+        if (active) phase2_merge(s, sm);
         __threadfence();
         cluster_barrier();
-        if (active) phase3_flatten(s, par);
+        if (active) phase3_flatten(s, sm.par);
         __syncthreads();  // shared memory is reused by the next item
     }
 }

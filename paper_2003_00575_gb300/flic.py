@@ -25,7 +25,7 @@ FLIC_ERR_BUSY = 5
 FLIC_ERR_UNSUPPORTED = 6
 FLIC_FLAG_NO_WRAP = 1
 FLIC_MAX_PIXELS = 1 << 19
-FLIC_MAX_ROWS = 1024
+FLIC_MAX_ROWS = 512
 FLIC_MAX_SKIP = 8
 
 # every symbol include/flic.h declares, with (restype, argtypes)

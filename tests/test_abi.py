@@ -77,7 +77,7 @@ def test_strip_planner_invariants(lib_path, seed):
     import numpy as np
     from paper_2003_00575_gb300 import flic
     g = np.random.default_rng(seed)
-    R = int(g.integers(1, 1025))
+    R = int(g.integers(1, 513))
     C = int(g.integers(1, max(2, (1 << 19) // R + 1)))
     S = int(g.integers(1, 9))
     px = int(g.choice([64, 1024, 4096, 16384, 32768]))
@@ -95,3 +95,6 @@ def test_strip_planner_invariants(lib_path, seed):
         assert W % 4 == 0 and W >= S and last >= S
     assert P >= max(W, 32) and P & (P - 1) == 0
     assert R * P <= 32768
+    rp = (W + S + 3) // 4 * 4
+    assert 4 * R * max(rp, P) + 2 * R * P + 8 * R * (P // 32) + 64 == p["smem"]
+    assert p["smem"] <= 227 * 1024 - 256

@@ -237,6 +237,33 @@ flic_status flic_device_status(flic_handle h, int32_t clear);
  */
 flic_status flic_debug_set_iter_limit(flic_handle h, int32_t limit);
 
+/*
+ * flic_project_noalloc — flic_project for callers that cannot allocate device memory
+ * (the paper has no counterpart; this is an integration entry point).  Some callers may
+ * only use the buffers they are handed: code running inside a host framework whose
+ * device memory belongs to its own pool, or plugins that must not call cudaMalloc.  This
+ * call needs no handle and allocates nothing: its working memory (the 64-bit per-pixel
+ * keys and the boundary tables) lives in static device arrays of fixed size inside
+ * libflic, held by every GPU that loads the library until the process exits (about
+ * 2.1 MiB).
+ *   rows, cols   2 <= rows <= FLIC_MAX_ROWS, cols <= FLIC_NOALLOC_MAX_COLS,
+ *                rows*cols <= FLIC_NOALLOC_MAX_PIXELS; larger shapes give FLIC_ERR_INVALID
+ *   elevation    host, rows doubles (radians, any order, distinct); az_step as in
+ *                flic_create (cols*az_step must be 2*pi: FLIC_ERR_UNSUPPORTED otherwise)
+ *   xyz, n, range_out, point_pixel, stream: as in flic_project (range_out is required)
+ * Results are identical to flic_project on a handle of the same geometry.  The first call
+ * on each device looks up the static arrays' device addresses (cudaGetSymbolAddress) with
+ * that device current, so make it before any stream capture.  Each call copies the tables
+ * from host memory on `stream` and clears the keys it uses; all calls share the arrays, so
+ * calls that overlap on the GPU (other streams or threads) race and must be serialised by
+ * the caller.  Errors: FLIC_ERR_INVALID, FLIC_ERR_UNSUPPORTED, FLIC_ERR_CUDA.
+ */
+#define FLIC_NOALLOC_MAX_PIXELS (1 << 18)
+#define FLIC_NOALLOC_MAX_COLS 8192
+flic_status flic_project_noalloc(int32_t rows, int32_t cols, const double* elevation,
+                                 double az_step, const float* xyz, int64_t n, float* range_out,
+                                 int32_t* point_pixel, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

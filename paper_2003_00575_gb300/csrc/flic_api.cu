@@ -117,6 +117,8 @@ int usable_cluster(int want, int threads, size_t smem) {
 
 }  // namespace
 
+void flic::set_last_error(const char* msg) { g_err = msg; }
+
 struct flic_ctx {
     int R = 0, C = 0, S = 0;
     float delta = 0.0f, delta2 = 0.0f;

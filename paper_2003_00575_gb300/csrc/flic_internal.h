@@ -82,6 +82,9 @@ cudaError_t launch_project(const ProjDesc& P, const float* xyz, int64_t n,
                            unsigned long long* keys, int32_t* point_pixel, cudaStream_t stream);
 cudaError_t launch_decode(const ProjDesc& P, const unsigned long long* keys, float* range_out,
                           cudaStream_t stream);
+// Sets the thread-local message returned by flic_last_error().
+void set_last_error(const char* msg);
+
 cudaError_t launch_scatter(const int32_t* labels, int64_t npix, const int32_t* point_pixel,
                            int64_t n, int32_t* point_labels, cudaStream_t stream);
 

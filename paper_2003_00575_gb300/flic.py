@@ -27,6 +27,8 @@ FLIC_FLAG_NO_WRAP = 1
 FLIC_MAX_PIXELS = 1 << 19
 FLIC_MAX_ROWS = 512
 FLIC_MAX_SKIP = 8
+FLIC_NOALLOC_MAX_PIXELS = 1 << 18
+FLIC_NOALLOC_MAX_COLS = 8192
 
 # every symbol include/flic.h declares, with (restype, argtypes)
 _P = ctypes.c_void_p
@@ -57,6 +59,7 @@ SIGNATURES = {
     "flic_batch_last_plan": (_I32, [_P, _P]),
     "flic_device_status": (_I32, [_P, _I32]),
     "flic_debug_set_iter_limit": (_I32, [_P, _I32]),
+    "flic_project_noalloc": (_I32, [_I32, _I32, _P, _F64, _P, _I64, _P, _P, _P]),
 }
 
 
@@ -282,3 +285,15 @@ def flic_device_status(h: Handle, clear: bool = True) -> int:
 
 def flic_debug_set_iter_limit(h: Handle, limit: int) -> None:
     _check(_lib.flic_debug_set_iter_limit(h.ptr, limit))
+
+
+def flic_project_noalloc(rows: int, cols: int, elevation, az_step: float, xyz, range_out,
+                         point_pixel, stream=None) -> None:
+    """flic_project without a handle or any allocation (static working memory in libflic)."""
+    elev = np.ascontiguousarray(elevation, dtype=np.float64)
+    n = xyz.numel() // 3
+    _check(_lib.flic_project_noalloc(rows, cols, elev.ctypes.data, float(az_step),
+                                     _dptr(xyz, "float32", 3 * n, "xyz"), n,
+                                     _dptr(range_out, "float32", rows * cols, "range_out"),
+                                     _dptr(point_pixel, "int32", n, "point_pixel"),
+                                     _stream(stream)))

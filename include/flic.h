@@ -24,7 +24,10 @@
  *     and flic_device_status synchronise.
  *   - Nothing throws across the ABI.  Each call returns a flic_status; on a non-OK
  *     status flic_last_error() returns a thread-local message describing it.
- *   - A handle is not thread-safe: use one handle per sensor and per host thread.
+ *   - A handle is not thread-safe: use one handle per sensor and per host thread.  Calls
+ *     on one handle (or one batch object) must not overlap on the GPU: their launches
+ *     share the object's working memory (task counters, projection keys), so issue them
+ *     on one stream or order them with events.
  *
  * Edge predicate (identical on every path; fixed here so that results are exact):
  *   valid(x)  :=  x > 0 and x finite            (0, negative, NaN, inf are "no return")
@@ -68,9 +71,9 @@ typedef enum {
 #define FLIC_FLAG_NO_WRAP 0x1u  /* columns do not wrap (sensor covers < 360 deg azimuth) */
 
 /* Largest frame the labeller accepts: rows * cols <= FLIC_MAX_PIXELS, rows <= FLIC_MAX_ROWS.
- * A frame is split into at most 16 full-height column strips of at most 32768 (padded)
+ * A frame is split into at most 64 full-height column strips of at most 32768 (padded)
  * pixels each; a shape that does not fit gives FLIC_ERR_UNSUPPORTED from flic_create. */
-#define FLIC_MAX_PIXELS (1 << 19)
+#define FLIC_MAX_PIXELS (1 << 21)
 #define FLIC_MAX_ROWS 512
 #define FLIC_MAX_SKIP 8
 
@@ -194,24 +197,26 @@ flic_status flic_batch_destroy(flic_batch b);
 
 /*
  * Launch-shape tuning (no counterpart in the paper).  px_per_cta: target pixels per
- * thread block strip (the tile of the shared-memory union pass), 0 = built-in default;
- * threads: threads per block (128..1024, multiple of 32), 0 = default;
- * cluster: max thread blocks cooperating on one frame (1..16), 0 = default.
- * flic_set_tuning applies to the handle's single-frame calls, flic_batch_set_tuning to
- * a batch object.  Results never depend on these values.  Errors: FLIC_ERR_INVALID.
+ * strip, the tile of the shared-memory union pass (0 = built-in default, 16384);
+ * threads: threads per block (128..512, multiple of 32; 0 = 512); max_strips: upper
+ * bound on the strips one frame is split into (1..64; 0 = 64); ctas_per_sm (batch only):
+ * cap on resident blocks per SM (0 = as many as fit).  flic_set_tuning applies to the
+ * handle's single-frame calls, flic_batch_set_tuning to a batch object.  Results never
+ * depend on these values.  Errors: FLIC_ERR_INVALID, FLIC_ERR_UNSUPPORTED (the frame
+ * does not fit the requested shape; the previous tuning stays).
  */
-flic_status flic_set_tuning(flic_handle h, int32_t px_per_cta, int32_t threads, int32_t cluster);
+flic_status flic_set_tuning(flic_handle h, int32_t px_per_cta, int32_t threads, int32_t max_strips);
 flic_status flic_batch_set_tuning(flic_batch b, int32_t px_per_cta, int32_t threads,
-                                  int32_t cluster, int32_t ctas_per_sm);
+                                  int32_t max_strips, int32_t ctas_per_sm);
 
 /*
  * flic_plan_info — the handle's single-frame launch shape (no counterpart in the paper):
- *   info  host, 5 ints: strips (= blocks = cluster size), strip width, shared-memory row
- *         pitch, shared-memory bytes per block, threads per block.
+ *   info  host, 5 ints: strips, strip width, shared-memory row pitch, shared-memory bytes
+ *         per block, threads per block.
  * flic_batch_last_plan — shape of the last flic_label_batch launch:
- *   info  host, 8 ints: work items, clusters launched (persistent grid), blocks per
- *         cluster, threads per block, shared-memory bytes per block, strips over all
- *         frames, frames, 0.
+ *   info  host, 8 ints: queued tasks, blocks launched (persistent grid), max strips per
+ *         frame, threads per block, shared-memory bytes per block, strips over all frames,
+ *         frames, blocks that fit at once.
  */
 flic_status flic_plan_info(flic_handle h, int32_t* info);
 
@@ -221,7 +226,7 @@ flic_status flic_plan_info(flic_handle h, int32_t* info);
  * shared-memory bytes per block.  Errors: INVALID, UNSUPPORTED (does not fit).
  */
 flic_status flic_plan_frame(int32_t rows, int32_t cols, int32_t skip, int32_t px_per_cta,
-                            int32_t max_cluster, int32_t* info);
+                            int32_t max_strips, int32_t* info);
 flic_status flic_batch_last_plan(flic_batch b, int32_t* info);
 
 /*

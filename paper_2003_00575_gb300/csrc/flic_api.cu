@@ -14,10 +14,6 @@
 #include "flic.h"
 #include "flic_internal.h"
 
-namespace flic {
-cudaError_t max_active_clusters(int cluster, int threads, size_t smem, int* out);
-}
-
 namespace {
 
 thread_local std::string g_err;
@@ -38,13 +34,13 @@ flic_status cuda_fail(cudaError_t e, const char* what) {
 }
 
 constexpr double kTwoPi = 6.283185307179586476925286766559;
-constexpr int kMaxPaddedStrip = 32768;  // rows * pitch of one strip (16-bit keys, see kernel)
+constexpr int kMaxPaddedStrip = flic::kMaxStripPixels;
 
 struct Tuning {
     int px_per_cta = 16384;
     int threads = 512;
-    int cluster = flic::kMaxCluster;
-    int ctas_per_sm = 0;  // batch only: 0 = as many as fit
+    int max_strips = flic::kMaxStrips;
+    int ctas_per_sm = 0;  // 0 = as many as fit
 };
 
 struct StripPlan {
@@ -63,15 +59,15 @@ int pow2_log2_ceil(int x) {
 }
 
 // Split a rows x cols frame into full-height column strips: about px_target pixels each,
-// at most max_cluster strips, widths a multiple of 4 (aligned vector access), every strip
+// at most max_strips strips, widths a multiple of 4 (aligned vector access), every strip
 // at least `skip` wide when there are several (so an edge crosses at most one border),
 // and rows * pitch <= kMaxPaddedStrip with pitch = next power of two >= max(width, 32).
-bool plan_frame(int R, int C, int S, int px_target, int max_cluster, StripPlan* out) {
-    int n0 = std::max(1, std::min(max_cluster, ceil_div(std::max(1, R * C), std::max(1, px_target))));
+bool plan_frame(int R, int C, int S, int px_target, int max_strips, StripPlan* out) {
+    int n0 = std::max(1, std::min(max_strips, ceil_div(std::max(1, R * C), std::max(1, px_target))));
     // preferred strip count first, then more strips, then fewer; for each count a few
     // widths, so that a narrow last strip can be avoided
     std::vector<int> counts;
-    for (int n = n0; n <= max_cluster; ++n) counts.push_back(n);
+    for (int n = n0; n <= max_strips; ++n) counts.push_back(n);
     for (int n = n0 - 1; n >= 1; --n) counts.push_back(n);
     for (int n : counts) {
         for (int extra = 0; extra < 4; ++extra) {
@@ -105,14 +101,17 @@ int device_max_smem() {
     return v;
 }
 
-// Largest cluster size the device can schedule for the label kernel (16, else 8, ...).
-int usable_cluster(int want, int threads, size_t smem) {
-    for (int c = want; c >= 1; c /= 2) {
-        int n = 0;
-        if (flic::max_active_clusters(c, threads, smem, &n) == cudaSuccess && n > 0) return c;
+// Blocks of the label kernel that fit at once (all SMs), capped by ctas_per_sm if set.
+int resident_blocks(int threads, size_t smem, int ctas_per_sm) {
+    int dev = 0, nsm = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (flic::label_blocks_per_sm(threads, smem, &per) != cudaSuccess) {
         cudaGetLastError();
+        per = 1;
     }
-    return 1;
+    if (ctas_per_sm > 0) per = std::min(per, ctas_per_sm);
+    return std::max(1, per) * std::max(1, nsm);
 }
 
 }  // namespace
@@ -138,6 +137,8 @@ struct flic_ctx {
     float* d_range = nullptr;
     int32_t* d_status = nullptr;
     int iter_limit = 0;
+    int32_t* d_counters = nullptr;  // task queue of single-frame launches
+    int resident = 1;               // blocks of the label kernel that fit at once
     Tuning tune;
     StripPlan plan;
     uint64_t uid = 0;      // unique per handle ever created (pointers can be reused)
@@ -146,17 +147,19 @@ struct flic_ctx {
 
 struct flic_batch_ctx {
     int max_frames = 0;
+    int max_tasks = 0;
     int device = 0;
     flic::FrameDesc* h_frames = nullptr;  // pinned staging
-    flic::ItemDesc* h_items = nullptr;
+    flic::Task* h_tasks = nullptr;
     flic::FrameDesc* d_frames = nullptr;
-    flic::ItemDesc* d_items = nullptr;
+    flic::Task* d_tasks = nullptr;
+    int32_t* d_counters = nullptr;
     cudaEvent_t staged = nullptr;       // descriptor upload done: staging reusable
     cudaEvent_t kernel_done = nullptr;  // last launch done: device descriptors reusable
     bool pending = false;
     cudaStream_t cap_stream = nullptr;
     Tuning tune;
-    std::map<std::tuple<int, int, int, int, size_t>, cudaGraphExec_t> graphs;
+    std::map<std::tuple<int, int, int, int, size_t>, cudaGraphExec_t> graphs;  // ntasks, nframes, grid, threads, smem
     int last_info[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // the previous call's arguments and launch shape: an identical call replays the graph
     std::vector<const void*> last_args;
@@ -263,24 +266,17 @@ void free_ctx(flic_ctx* h) {
     cudaFree(h->d_keys);
     cudaFree(h->d_range);
     cudaFree(h->d_status);
+    cudaFree(h->d_counters);
     delete h;
 }
 
 flic_status replan(flic_ctx* h) {
     StripPlan pl;
-    int cap = h->tune.cluster;
-    if (!plan_frame(h->R, h->C, h->S, h->tune.px_per_cta, cap, &pl))
+    if (!plan_frame(h->R, h->C, h->S, h->tune.px_per_cta, h->tune.max_strips, &pl))
         return fail(FLIC_ERR_UNSUPPORTED, "frame %dx%d (skip %d) does not fit %d strips",
-                    h->R, h->C, h->S, cap);
-    if (pl.nstrips > 1) {
-        int c = usable_cluster(pl.nstrips, h->tune.threads, pl.smem);
-        if (c < pl.nstrips) {
-            if (!plan_frame(h->R, h->C, h->S, h->tune.px_per_cta, c, &pl))
-                return fail(FLIC_ERR_UNSUPPORTED, "frame %dx%d needs a cluster of %d blocks",
-                            h->R, h->C, pl.nstrips);
-        }
-    }
+                    h->R, h->C, h->S, h->tune.max_strips);
     h->plan = pl;
+    h->resident = resident_blocks(h->tune.threads, pl.smem, h->tune.ctas_per_sm);
     return FLIC_OK;
 }
 
@@ -335,6 +331,8 @@ flic_status flic_create_ex(int32_t rows, int32_t cols, const double* elevation, 
     if ((st = upload(&h->d_kh, h->h_kh, "Kh table")) != FLIC_OK) { free_ctx(h); return st; }
     std::vector<int32_t> zero(1, 0);
     if ((st = upload(&h->d_status, zero, "status word")) != FLIC_OK) { free_ctx(h); return st; }
+    std::vector<int32_t> zeros(flic::counter_ints(1), 0);
+    if ((st = upload(&h->d_counters, zeros, "task counters")) != FLIC_OK) { free_ctx(h); return st; }
 
     std::vector<float> colb, rowb;
     std::vector<int32_t> srow;
@@ -378,14 +376,14 @@ flic_status flic_get_tables(flic_handle h, float* kv, float* kh) {
 }
 
 flic_status flic_plan_frame(int32_t rows, int32_t cols, int32_t skip, int32_t px_per_cta,
-                            int32_t max_cluster, int32_t* info) {
+                            int32_t max_strips, int32_t* info) {
     if (!info || rows < 1 || cols < 1 || skip < 1 || skip > FLIC_MAX_SKIP || px_per_cta < 1 ||
-        max_cluster < 1 || max_cluster > flic::kMaxCluster)
+        max_strips < 1 || max_strips > flic::kMaxStrips)
         return fail(FLIC_ERR_INVALID, "bad argument");
     StripPlan pl;
-    if (!plan_frame(rows, cols, skip, px_per_cta, max_cluster, &pl))
+    if (!plan_frame(rows, cols, skip, px_per_cta, max_strips, &pl))
         return fail(FLIC_ERR_UNSUPPORTED, "frame %dx%d does not fit %d strips", rows, cols,
-                    max_cluster);
+                    max_strips);
     info[0] = pl.nstrips;
     info[1] = pl.strip_w;
     info[2] = 1 << pl.pitch_log2;
@@ -416,11 +414,14 @@ flic_status flic_label(flic_handle h, const float* range, int32_t* labels, void*
     if ((const void*)range == (const void*)labels) return fail(FLIC_ERR_INVALID, "range aliases labels");
     flic::LabelLaunch L{};
     L.frames = nullptr;
-    L.items = nullptr;
-    L.nitems = 1;
-    L.cluster = h->plan.nstrips;
+    L.tasks = nullptr;
     L.single = frame_desc(h, range, labels, h->plan);
-    cudaError_t e = flic::launch_label(L, 1, h->tune.threads, h->plan.smem, (cudaStream_t)stream);
+    const bool border = h->plan.nstrips > 1 || h->wrap;
+    L.ntasks = h->plan.nstrips * (border ? 2 : 1);
+    L.nframes = 1;
+    L.counters = h->d_counters;
+    const int grid = std::min(L.ntasks, h->resident);
+    cudaError_t e = flic::launch_label(L, grid, h->tune.threads, h->plan.smem, (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "flic_label launch");
     return FLIC_OK;
 }
@@ -463,16 +464,16 @@ flic_status flic_scatter(flic_handle h, const int32_t* labels, const int32_t* po
     return FLIC_OK;
 }
 
-flic_status flic_set_tuning(flic_handle h, int32_t px_per_cta, int32_t threads, int32_t cluster) {
+flic_status flic_set_tuning(flic_handle h, int32_t px_per_cta, int32_t threads, int32_t max_strips) {
     if (!h) return fail(FLIC_ERR_INVALID, "NULL handle");
-    if (px_per_cta < 0 || threads < 0 || cluster < 0 || cluster > flic::kMaxCluster ||
-        (threads && (threads < 128 || threads > 1024 || threads % 32)))
+    if (px_per_cta < 0 || threads < 0 || max_strips < 0 || max_strips > flic::kMaxStrips ||
+        (threads && (threads < 128 || threads > 512 || threads % 32)))
         return fail(FLIC_ERR_INVALID, "bad tuning values");
     Tuning old = h->tune;
     Tuning def;
     h->tune.px_per_cta = px_per_cta ? px_per_cta : def.px_per_cta;
     h->tune.threads = threads ? threads : def.threads;
-    h->tune.cluster = cluster ? cluster : def.cluster;
+    h->tune.max_strips = max_strips ? max_strips : def.max_strips;
     flic_status st = replan(h);
     if (st != FLIC_OK) {
         h->tune = old;
@@ -491,6 +492,8 @@ flic_status flic_device_status(flic_handle h, int32_t clear) {
     if (clear) {
         int32_t z = 0;
         e = cudaMemcpy(h->d_status, &z, sizeof(z), cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemset(h->d_counters, 0, sizeof(int32_t) * flic::counter_ints(1));
         if (e != cudaSuccess) return cuda_fail(e, "flic_device_status clear");
     }
     if (v != 0) return fail(FLIC_ERR_TIMEOUT, "a bounded device loop gave up (status %d)", v);
@@ -513,14 +516,18 @@ flic_status flic_batch_create(int32_t max_frames, flic_batch* out) {
         return fail(FLIC_ERR_INVALID, "max_frames must be 1..32768");
     flic_batch_ctx* b = new flic_batch_ctx();
     b->max_frames = max_frames;
+    b->max_tasks = 2 * flic::kMaxStrips * max_frames;
     cudaGetDevice(&b->device);
     cudaError_t e;
     size_t fb = sizeof(flic::FrameDesc) * (size_t)max_frames;
-    size_t ib = sizeof(flic::ItemDesc) * (size_t)max_frames;
+    size_t tb = sizeof(flic::Task) * (size_t)b->max_tasks;
+    size_t cb = sizeof(int32_t) * flic::counter_ints(max_frames);
     if ((e = cudaHostAlloc((void**)&b->h_frames, fb, cudaHostAllocDefault)) != cudaSuccess ||
-        (e = cudaHostAlloc((void**)&b->h_items, ib, cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaHostAlloc((void**)&b->h_tasks, tb, cudaHostAllocDefault)) != cudaSuccess ||
         (e = cudaMalloc((void**)&b->d_frames, fb)) != cudaSuccess ||
-        (e = cudaMalloc((void**)&b->d_items, ib)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&b->d_tasks, tb)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&b->d_counters, cb)) != cudaSuccess ||
+        (e = cudaMemset(b->d_counters, 0, cb)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->kernel_done, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -547,9 +554,10 @@ flic_status flic_batch_destroy(flic_batch b) {
     cudaError_t e = cudaDeviceSynchronize();
     clear_graphs(b);
     if (b->h_frames) cudaFreeHost(b->h_frames);
-    if (b->h_items) cudaFreeHost(b->h_items);
+    if (b->h_tasks) cudaFreeHost(b->h_tasks);
     cudaFree(b->d_frames);
-    cudaFree(b->d_items);
+    cudaFree(b->d_tasks);
+    cudaFree(b->d_counters);
     if (b->staged) cudaEventDestroy(b->staged);
     if (b->kernel_done) cudaEventDestroy(b->kernel_done);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -559,16 +567,16 @@ flic_status flic_batch_destroy(flic_batch b) {
 }
 
 flic_status flic_batch_set_tuning(flic_batch b, int32_t px_per_cta, int32_t threads,
-                                  int32_t cluster, int32_t ctas_per_sm) {
+                                  int32_t max_strips, int32_t ctas_per_sm) {
     if (!b) return fail(FLIC_ERR_INVALID, "NULL batch");
-    if (px_per_cta < 0 || threads < 0 || cluster < 0 || cluster > flic::kMaxCluster ||
-        ctas_per_sm < 0 || (threads && (threads < 128 || threads > 1024 || threads % 32)))
+    if (px_per_cta < 0 || threads < 0 || max_strips < 0 || max_strips > flic::kMaxStrips ||
+        ctas_per_sm < 0 || (threads && (threads < 128 || threads > 512 || threads % 32)))
         return fail(FLIC_ERR_INVALID, "bad tuning values");
     if (b->pending) cudaEventSynchronize(b->kernel_done);
     Tuning def;
     b->tune.px_per_cta = px_per_cta ? px_per_cta : def.px_per_cta;
     b->tune.threads = threads ? threads : def.threads;
-    b->tune.cluster = cluster ? cluster : def.cluster;
+    b->tune.max_strips = max_strips ? max_strips : def.max_strips;
     b->tune.ctas_per_sm = ctas_per_sm;
     clear_graphs(b);
     return FLIC_OK;
@@ -607,6 +615,9 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
         args.push_back(labels[i]);
     }
     if (b->last_exec && args == b->last_args) {
+        // the queue counters are shared with the previous launch: order after it
+        e = cudaStreamWaitEvent(st, b->kernel_done, 0);
+        if (e != cudaSuccess) return cuda_fail(e, "stream wait");
         e = cudaGraphLaunch(b->last_exec, st);
         if (e != cudaSuccess) return cuda_fail(e, "graph launch");
         e = cudaEventRecord(b->kernel_done, st);
@@ -621,68 +632,50 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
     }
     const Tuning& t = b->tune;
 
-    // cluster size this device schedules at the largest strip footprint
     std::vector<StripPlan> plans(nframes);
     size_t smem = 0;
-    int cluster = t.cluster;
-    for (int pass = 0; pass < 2; ++pass) {
-        smem = 0;
-        for (int i = 0; i < nframes; ++i) {
-            const flic_ctx* h = hs[i];
-            if (!plan_frame(h->R, h->C, h->S, t.px_per_cta, cluster, &plans[i]))
-                return fail(FLIC_ERR_UNSUPPORTED, "frame %d (%dx%d) does not fit %d strips", i,
-                            h->R, h->C, cluster);
-            smem = std::max(smem, plans[i].smem);
-        }
-        int c = usable_cluster(cluster, t.threads, smem);
-        if (c == cluster) break;
-        cluster = c;
+    int total_strips = 0;
+    for (int i = 0; i < nframes; ++i) {
+        const flic_ctx* h = hs[i];
+        if (!plan_frame(h->R, h->C, h->S, t.px_per_cta, t.max_strips, &plans[i]))
+            return fail(FLIC_ERR_UNSUPPORTED, "frame %d (%dx%d) does not fit %d strips", i, h->R,
+                        h->C, t.max_strips);
+        smem = std::max(smem, plans[i].smem);
+        total_strips += plans[i].nstrips;
+        b->h_frames[i] = frame_desc(h, ranges[i], labels[i], plans[i]);
     }
+    const int resident = resident_blocks(t.threads, smem, t.ctas_per_sm);
 
-    // first-fit decreasing: frames with more strips first, each frame's strips on
-    // consecutive ranks of one item
+    // the queue: P1 tasks of the frames, largest first; P3 tasks of a frame about two waves
+    // of blocks after its last P1 task (one wave is one P1 task's duration, so a frame's
+    // P3 tasks would arrive just as it finishes), so that they seldom wait
     std::vector<int> order(nframes);
     for (int i = 0; i < nframes; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(),
-                     [&](int a, int c) { return plans[a].nstrips > plans[c].nstrips; });
-    for (int i = 0; i < nframes; ++i) b->h_frames[i] = frame_desc(hs[i], ranges[i], labels[i], plans[i]);
-    std::vector<int> used;  // ranks used per item
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        return (int64_t)hs[a]->R * hs[a]->C > (int64_t)hs[c]->R * hs[c]->C;
+    });
+    int nt = 0;
+    std::vector<std::pair<int, int>> pending;  // (P1 count after which to emit, frame)
+    size_t next_pending = 0;
+    auto emit_p3 = [&](int fi) {
+        for (int si = 0; si < plans[fi].nstrips; ++si)
+            b->h_tasks[nt++] = flic::Task{fi, (int16_t)si, (int16_t)flic::kTaskP3};
+    };
+    int p1_count = 0;
     for (int oi = 0; oi < nframes; ++oi) {
         const int fi = order[oi];
-        const int ns = plans[fi].nstrips;
-        size_t it = 0;
-        while (it < used.size() && used[it] + ns > cluster) ++it;
-        if (it == used.size()) {
-            used.push_back(0);
-            flic::ItemDesc& d = b->h_items[it];
-            for (int q = 0; q < flic::kMaxCluster; ++q) {
-                d.frame[q] = -1;
-                d.strip[q] = 0;
-            }
+        for (int si = 0; si < plans[fi].nstrips; ++si) {
+            b->h_tasks[nt++] = flic::Task{fi, (int16_t)si, (int16_t)flic::kTaskP1};
+            ++p1_count;
+            while (next_pending < pending.size() && pending[next_pending].first <= p1_count)
+                emit_p3(pending[next_pending++].second);
         }
-        flic::ItemDesc& d = b->h_items[it];
-        for (int s = 0; s < ns; ++s) {
-            d.frame[used[it] + s] = (int16_t)fi;
-            d.strip[used[it] + s] = (int16_t)s;
-        }
-        used[it] += ns;
+        const bool border = plans[fi].nstrips > 1 || hs[fi]->wrap;
+        if (border) pending.push_back({p1_count + 2 * resident, fi});
     }
-    const int nitems = (int)used.size();
-
-    int active = 0;
-    e = flic::max_active_clusters(cluster, t.threads, smem, &active);
-    if (e != cudaSuccess || active < 1) {
-        cudaGetLastError();
-        return fail(FLIC_ERR_UNSUPPORTED, "no cluster of %d blocks with %zu B shared memory fits",
-                    cluster, smem);
-    }
-    if (t.ctas_per_sm > 0) {
-        int dev = 0, nsm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-        active = std::max(1, std::min(active, nsm * t.ctas_per_sm / cluster));
-    }
-    const int grid = std::min(nitems, active);
+    while (next_pending < pending.size()) emit_p3(pending[next_pending++].second);
+    const int ntasks = nt;
+    const int grid = std::min(ntasks, resident);
 
     // descriptors: the previous kernel (on whatever stream) must be done reading them
     if (b->pending) {
@@ -692,14 +685,14 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
     e = cudaMemcpyAsync(b->d_frames, b->h_frames, sizeof(flic::FrameDesc) * nframes,
                         cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->d_items, b->h_items, sizeof(flic::ItemDesc) * nitems,
+        e = cudaMemcpyAsync(b->d_tasks, b->h_tasks, sizeof(flic::Task) * ntasks,
                             cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(b->staged, st);
     if (e != cudaSuccess) return cuda_fail(e, "descriptor upload");
     b->pending = true;
 
     // the persistent kernel, captured once per launch shape and replayed
-    auto key = std::make_tuple(nitems, grid, cluster, t.threads, smem);
+    auto key = std::make_tuple(ntasks, nframes, grid, t.threads, smem);
     auto found = b->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     if (found != b->graphs.end()) {
@@ -710,9 +703,10 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
         if (e != cudaSuccess) return cuda_fail(e, "graph capture begin");
         flic::LabelLaunch L{};
         L.frames = b->d_frames;
-        L.items = b->d_items;
-        L.nitems = nitems;
-        L.cluster = cluster;
+        L.tasks = b->d_tasks;
+        L.ntasks = ntasks;
+        L.nframes = nframes;
+        L.counters = b->d_counters;
         cudaError_t le = flic::launch_label(L, grid, t.threads, smem, b->cap_stream);
         e = cudaStreamEndCapture(b->cap_stream, &graph);
         if (le != cudaSuccess) {
@@ -731,9 +725,8 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
     if (e != cudaSuccess) return cuda_fail(e, "event record");
     b->last_args.swap(args);
     b->last_exec = exec;
-    int total_ctas = 0;
-    for (int i = 0; i < nframes; ++i) total_ctas += plans[i].nstrips;
-    int info[8] = {nitems, grid, cluster, t.threads, (int)smem, total_ctas, nframes, 0};
+    int info[8] = {ntasks, grid, t.max_strips, t.threads, (int)smem, total_strips, nframes,
+                   resident};
     std::memcpy(b->last_info, info, sizeof(info));
     return FLIC_OK;
 }

@@ -10,8 +10,8 @@
 namespace flic {
 
 constexpr int kMaxSkip = 8;
-constexpr int kMaxCluster = 16;          // thread blocks that cooperate on one work item
-constexpr int kMaxStripPixels = 65535;   // local indices (and the run-merge keys) use 16 bits
+constexpr int kMaxStrips = 64;           // column strips per frame
+constexpr int kMaxStripPixels = 32768;   // rows * pitch of one strip (16-bit match keys)
 constexpr int kDefaultIterLimit = 1 << 20;
 
 // One frame as the labelling kernel sees it.  The strip decomposition is part of the
@@ -25,25 +25,40 @@ struct FrameDesc {
     int32_t rows, cols, skip;
     float delta2;         // delta*delta in fp32
     int32_t wrap;         // 1: column cols-1 neighbours column 0
-    int32_t nstrips;      // thread blocks (strips) the frame is split into
+    int32_t nstrips;      // strips the frame is split into
     int32_t strip_w;      // columns per strip (last strip may be narrower)
     int32_t pitch_log2;   // local row pitch of the shared-memory forest = 1 << pitch_log2
     int32_t iter_limit;   // bound of every device loop; 0 -> kDefaultIterLimit
     int32_t pad_;
 };
 
-// A work item: up to kMaxCluster (frame, strip) pairs processed by one thread-block
-// cluster between two cluster barriers.  frame < 0 marks an idle block.
-struct ItemDesc {
-    int16_t frame[kMaxCluster];
-    int16_t strip[kMaxCluster];
+// One queue entry: P1 (stage, edges, strip-local labels) or P3 (flatten) of one strip.
+constexpr int32_t kTaskP1 = 0;
+constexpr int32_t kTaskP3 = 1;
+struct Task {
+    int32_t frame;
+    int16_t strip;
+    int16_t kind;
 };
+
+// Queue counters (int32, zero between launches; the kernel's last block re-zeroes them):
+// [kCtrNext] next task, [kCtrExit] blocks done, then kCtrPerFrame per frame f at
+// kCtrFrames + kCtrPerFrame*f: [0] borders merged, [1] frame ready for P3,
+// [2 + b] strips of border b that finished P1.
+constexpr int kCtrNext = 0;
+constexpr int kCtrExit = 1;
+constexpr int kCtrFrames = 2;
+constexpr int kCtrPerFrame = 2 + kMaxStrips;
+__host__ __device__ inline size_t counter_ints(int nframes) {
+    return size_t(kCtrFrames) + size_t(kCtrPerFrame) * size_t(nframes);
+}
 
 struct LabelLaunch {
     const FrameDesc* frames;   // device array (batch), or nullptr: use `single`
-    const ItemDesc* items;     // device array (batch), or nullptr: one item, rank = strip
-    int32_t nitems;
-    int32_t cluster;           // blocks per cluster (== blocks per item)
+    const Task* tasks;         // device array (batch), or nullptr: implicit single-frame queue
+    int32_t ntasks;
+    int32_t nframes;
+    int32_t* counters;         // counter_ints(nframes), zero at launch
     FrameDesc single;
 };
 
@@ -65,8 +80,9 @@ inline size_t strip_smem_bytes(int rows, int pitch_log2, int width, int skip) {
 constexpr size_t kMaxDynSmem = 227 * 1024 - 256;
 
 // Kernel launchers (flic_label.cu / flic_project.cu).  Return cudaGetLastError().
-cudaError_t launch_label(const LabelLaunch& L, int grid_clusters, int threads, size_t smem,
+cudaError_t launch_label(const LabelLaunch& L, int grid, int threads, size_t smem,
                          cudaStream_t stream);
+cudaError_t label_blocks_per_sm(int threads, size_t smem, int* out);
 cudaError_t launch_edges(const FrameDesc& f, uint16_t* mask, cudaStream_t stream);
 cudaError_t label_kernel_setup(size_t max_smem);
 

@@ -1,46 +1,48 @@
 // flic_label.cu — the FLIC neighbour test and connected-component labelling on sm_103a.
 //
-// One thread-block cluster labels one work item: up to kMaxCluster full-height column
-// strips of one or more frames.  Each block owns one strip (rows x W columns) and runs:
+// One persistent kernel drains a queue of tasks.  A frame is split into full-height
+// column strips; each strip gives two tasks.
 //
-//   phase 1  (edge test + tile-local union, in shared memory)
-//            0. the strip's range readings, plus S halo columns on the right (wrapping to
-//               column 0 at the seam), are staged into shared memory: one TMA bulk copy
-//               (cp.async.bulk) per row completing on an mbarrier, or plain loads when the
-//               frame is not 16-byte aligned;
-//            1. every pixel's 2S edge bits (Eq. 2/3; offsets 1..S right and down, the
-//               Map Connections of §III-B-2) are computed from shared memory into a 16-bit
-//               mask per pixel; the staged readings are dead afterwards and their space
-//               becomes the parent array;
-//            a. each warp takes a 32-column row segment; the offset-1 right bits of the
-//               segment are gathered with __ballot_sync and every pixel's parent is set to
-//               the first pixel of its run, so a run of joined pixels becomes one star
-//               without a single atomic;
-//            b. the remaining in-strip edges — offset-1 links across segment borders,
-//               offsets 2..S along the row and 1..S down the column — are read from the
-//               masks; an edge whose two ends are already joined by runs is dropped with
-//               ballot bit tricks, lanes asking for the same union are merged with
-//               __match_any_sync, and the rest hook with shared-memory atomicMin (the
-//               smaller index becomes the root);
-//            c. paths are compressed by pointer jumping, so every pixel points at its
-//               strip-local root, the minimum index of its strip-local component;
-//            d. pixels in the first S columns publish their root in the frame's labels
-//               buffer, and roots of components touching either strip border publish
-//               themselves: these entries form the cross-strip forest.
-//   cluster barrier
-//   phase 2  (boundary merge, global memory): every edge that leaves the strip on the
-//            right (mask bits of offsets 1..S, including the azimuth wrap from the last
-//            column to the first) unites the two roots with atomicMin hooking and path
-//            halving.
-//   cluster barrier
-//   phase 3  (flatten): roots of border components look up their global root (read-only);
-//            every pixel then writes label = the minimum linear index of its component,
-//            or -1 for pixels that are not measurements.
+//   P1 (one block, one strip; edge test + tile-local union in shared memory)
+//      0. the strip's range readings, plus S halo columns on the right (wrapping to
+//         column 0 at the seam), are staged into shared memory: one TMA bulk copy
+//         (cp.async.bulk) per row completing on an mbarrier, or plain loads when the
+//         frame is not 16-byte aligned;
+//      1. every pixel's 2S edge bits (Eq. 2/3; offsets 1..S right and down, the Map
+//         Connections of §III-B-2) are computed from shared memory into a 16-bit mask
+//         per pixel; the staged readings are dead afterwards and their space becomes
+//         the parent array;
+//      a. each warp takes a 32-column row segment; the offset-1 right bits of the
+//         segment are gathered with __ballot_sync and every pixel's parent is set to
+//         the first pixel of its run, so a run of joined pixels becomes one star
+//         without a single atomic;
+//      b. bands of rows are walked top-down with the labels of the rows above in
+//         registers (phase1_bands below): runs hook under the label they touch, and
+//         only where labels meet is a union-find union made (__match_any_sync dedupe,
+//         shared-memory atomicMin hooking to the smaller index);
+//      c. segment seams: edges that cross a 32-column segment border inside the strip;
+//      d. every pixel's label is written as the global index of its strip-local root (a
+//         read-only walk up its short path), the minimum index of its strip-local
+//         component.
+//         A root's own entry is itself, so the labels buffer now holds a forest of
+//         depth one per strip: the cross-strip forest needs no other memory.
+//      The block that completes the last P1 task of a frame (atomic counter, fenced)
+//      then runs the frame's boundary merge:
+//   P2 (one block per frame; global memory): every edge that leaves a strip on the
+//      right (offsets 1..S, including the azimuth wrap from the last column to the
+//      first) unites the two strip-local roots with atomicMin hooking and path halving;
+//      rows that ask for the same pair of roots are merged in the warp first.  The
+//      block then raises the frame's ready flag.
+//   P3 (one block, one strip; flatten): waits for the frame's ready flag, then every
+//      pixel whose strip-local root was hooked by P2 gets the root of its tree (a
+//      read-only find): label = minimum linear index of the component; -1 stays -1.
 //
-// The labels buffer is the only global working memory: no scratch allocation.  No block
-// ever waits on another except at the two hardware cluster barriers, so the kernel has no
-// spin loop; every union and find loop is bounded by an iteration budget whose exhaustion
-// sets the frame's status word.
+// P3 tasks of a frame are queued about one wave of blocks after its P1 tasks, so they
+// seldom wait.  A block only ever waits for tasks that running blocks have already
+// taken and that never wait themselves, so the queue cannot deadlock; the wait is
+// bounded all the same and reports exhaustion in the frame's status word, as does every
+// union and find loop.  The last block to leave resets the queue's counters for the next
+// launch.  The labels buffer is the only global working memory besides those counters.
 #include <cstdint>
 
 #include "flic_device.cuh"
@@ -99,6 +101,14 @@ __device__ __forceinline__ void unite(int* par, int a, int b, const Strip& s) {
     int budget = s.limit;
     union_smem(par, a, b, budget);
     if (budget <= 0) report_timeout(s.status);
+}
+
+// Hook the run whose first pixel is `root` (a root, or hooked by this row already) under
+// label x < root: one atomicMin; if the pixel was already hooked elsewhere (old), the
+// two sets are united (the union-find retry step).
+__device__ __forceinline__ void hook(int* par, int root, int x, const Strip& s) {
+    const int old = atomicMin(par + root, x);
+    if (old != root && old != x) unite(par, old, x, s);
 }
 
 // b. every edge inside the strip that the runs do not already cover.  Each warp walks a
@@ -163,15 +173,15 @@ __device__ void phase1_bands(const Strip& s, const Carve& sm) {
                         multi |= cand != kInf && L != cand;
                         cand = min(cand, L);
                     }
-                } else {
-                    // from a row of the band above: plain union, unless lane l-1 has the
-                    // same edge and both rows join l-1 to l
+                } else if (inw) {
+                    // from a row of the band above (another warp): the upper pixel's
+                    // current parent is a member of its set, so it serves as its label
                     const int ia = ((r - k) << s.sh) + c;
-                    const bool e = inw && ((sm.mask[ia] >> (8 + k - 1)) & 1u);
-                    const unsigned em = __ballot_sync(kFull, e);
-                    const unsigned mb = sm.hmask[((r - k) << segs_log2) + seg];
-                    const unsigned implied = (em & m & mb) << 1;
-                    if (e && !((implied >> lane) & 1u)) unite(par, ia, i, s);
+                    if ((sm.mask[ia] >> (8 + k - 1)) & 1u) {
+                        const int L = ((volatile int*)par)[ia];
+                        multi |= cand != kInf && L != cand;
+                        cand = min(cand, L);
+                    }
                 }
             }
             const unsigned hasm = __ballot_sync(kFull, cand != kInf);
@@ -183,63 +193,69 @@ __device__ void phase1_bands(const Strip& s, const Carve& sm) {
                     if (va && (hasm & runbits)) {
                         mylab = X;
                         if (lane == st) {
-                            const int old = atomicMin(par + sidx, X);
-                            if (old != sidx && old != X) unite(par, old, X, s);
+                            hook(par, sidx, X, s);
                         } else {
-                            par[i] = X;  // shortcut for the compression pass
+                            par[i] = X;  // shortcut for the final walk to the root
                         }
                     }
                 } else {
-                    // several labels meet: one union per distinct (run, label) pair and
-                    // offset
-#pragma unroll
-                    for (int k = 1; k <= S; ++k) {
-                        if (r - k < r0) break;
-                        const int ck = ((mab[k - 1] >> (8 + k - 1)) & 1u) ? lab[k - 1] : kInf;
+                    // several labels meet.  Lanes are grouped by (run, label); each group's
+                    // first lane hooks the run's first pixel under the label with one
+                    // atomicMin, and only a hook that finds the pixel already hooked
+                    // elsewhere unites the two labels.  A lane with several different
+                    // labels above takes them one offset at a time.
+                    const unsigned anymulti = __ballot_sync(kFull, multi);
+                    if (!anymulti) {
                         const unsigned key =
-                            ck == kInf ? kFull : ((unsigned)st << 16) | (unsigned)ck;
+                            cand == kInf ? kFull : ((unsigned)st << 16) | (unsigned)cand;
                         const unsigned grp = __match_any_sync(kFull, key);
-                        if (ck != kInf && (__ffs(grp) - 1) == lane) unite(par, sidx, ck, s);
+                        if (cand != kInf && (__ffs(grp) - 1) == lane) hook(par, sidx, cand, s);
+                    } else {
+#pragma unroll
+                        for (int k = 1; k <= S; ++k) {
+                            if (r - k < 0) break;
+                            int ck = kInf;
+                            if (r - k >= r0) {
+                                if ((mab[k - 1] >> (8 + k - 1)) & 1u) ck = lab[k - 1];
+                            } else if (inw) {
+                                const int ia = ((r - k) << s.sh) + c;
+                                if ((sm.mask[ia] >> (8 + k - 1)) & 1u)
+                                    ck = ((volatile int*)par)[ia];
+                            }
+                            const unsigned key =
+                                ck == kInf ? kFull : ((unsigned)st << 16) | (unsigned)ck;
+                            const unsigned grp = __match_any_sync(kFull, key);
+                            if (ck != kInf && (__ffs(grp) - 1) == lane) hook(par, sidx, ck, s);
+                        }
                     }
                     __syncwarp();
-                    int root = 0;
-                    if (va && lane == st) {
-                        int budget = s.limit;
-                        root = find_smem(par, sidx, budget);
-                    }
-                    root = __shfl_sync(kFull, root, st);
+                    // the run's label: whatever its first pixel now points to
+                    const int lbl = (va && lane == st) ? ((volatile int*)par)[sidx] : 0;
+                    const int runlab = __shfl_sync(kFull, lbl, st);
                     if (va) {
-                        mylab = root;
-                        if (lane != st) par[i] = root;
+                        mylab = runlab;
+                        if (lane != st) par[i] = runlab;
                     }
                 }
             }
 
-            // offsets 2..S along the row
+            // offsets 2..S along the row, inside the segment (edges into the next
+            // segment are left to the seam pass); nothing to do when both runs already
+            // carry the same label
 #pragma unroll
             for (int k = 2; k <= S; ++k) {
-                const int stp = __shfl_down_sync(kFull, st, k);  // run start of lane + k
-                const bool e = ((mk >> (k - 1)) & 1u) && c + k < s.W;
-                const bool inseg = lane + k <= 31;
-                const bool e_in = e && inseg && stp != st;
+                const int stp = __shfl_down_sync(kFull, st, k);      // run start of lane + k
+                const int labp = __shfl_down_sync(kFull, mylab, k);  // its label
+                const bool e_in = ((mk >> (k - 1)) & 1u) && c + k < s.W && lane + k <= 31 &&
+                                  stp != st && labp != mylab;
                 const unsigned eb = __ballot_sync(kFull, e_in);
                 if (e_in) {
                     // implied by lane l-1 when l-1 ~ l and l-1+k ~ l+k by runs
                     const bool imp = lane > 0 && ((eb >> (lane - 1)) & 1u) &&
                                      ((m >> (lane - 1)) & 1u) && ((m >> (lane + k - 1)) & 1u);
                     if (!imp) unite(par, sidx, base + stp, s);
-                } else if (e && !inseg) {
-                    // into the next segment: covered when this run reaches lane 31, joins
-                    // lane 0 of the next segment, and the target lies in that first run
-                    const int t = lane + k - 32;
-                    const unsigned mn = sm.hmask[u + 1];
-                    const unsigned need_bits = (1u << t) - 1u;
-                    const bool joined = en == 31 && ((m >> 31) & 1u) && ((mn & need_bits) == need_bits);
-                    if (!joined) unite(par, i, i + k, s);
                 }
             }
-            // offset-1 link from lane 31 into the next segment (h1 implies c + 1 < W)
-            if (lane == 31 && ((m >> 31) & 1u)) unite(par, i, i + 1, s);
 
 #pragma unroll
             for (int k = S - 1; k > 0; --k) {
@@ -248,6 +264,87 @@ __device__ void phase1_bands(const Strip& s, const Carve& sm) {
             }
             lab[0] = mylab;
             mab[0] = mk;
+        }
+    }
+}
+
+// Edges that cross a 32-column segment border inside the strip (offsets 1..S to the
+// right), after the band pass.  Lanes are rows; the pair to unite is the current parents
+// of the two ends, and of consecutive rows asking for the same pair only the first asks.
+__device__ void phase1_seams(const Strip& s, const Carve& sm) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    volatile int* vp = sm.par;
+    const int nborders = (s.W - 1) >> 5;  // segment borders g | g+1 with (g+1)*32 < W
+    const int rblocks = (s.R + 31) >> 5;
+    for (int job = warp; job < nborders * rblocks; job += nwarps) {
+        const int g = job / rblocks;
+        const int r = ((job - g * rblocks) << 5) + lane;
+        const bool row_ok = r < s.R;
+        const int cb = (g + 1) << 5;  // first column of the next segment
+        int done_a = -1, done_b = -1;  // the last pair this lane united
+        for (int c = cb - s.S; c < cb; ++c) {
+            const unsigned mk = row_ok ? sm.mask[(r << s.sh) + c] : 0u;
+            for (int k = cb - c; k <= s.S; ++k) {
+                const bool e = ((mk >> (k - 1)) & 1u) && c + k < s.W;
+                int a = 0, b = 0;
+                if (e) {
+                    a = vp[(r << s.sh) + c];
+                    b = vp[(r << s.sh) + c + k];
+                }
+                const int pa = __shfl_up_sync(kFull, a, 1);
+                const int pb = __shfl_up_sync(kFull, b, 1);
+                const unsigned em = __ballot_sync(kFull, e);
+                const bool dup = (lane > 0 && ((em >> (lane - 1)) & 1u) && pa == a && pb == b) ||
+                                 (a == done_a && b == done_b);
+                if (e && !dup && a != b) {
+                    unite(sm.par, a, b, s);
+                    done_a = a;
+                    done_b = b;
+                }
+            }
+        }
+    }
+}
+
+// Edge bits of every pixel from the staged readings: bit k-1 = edge to the pixel k
+// columns right (into the halo at the strip's right edge), bit 8+k-1 = edge to the pixel
+// k rows down; validity as one ballot word per 32-column segment.
+template <int S>
+__device__ void mask_rows(const Strip& s, const Carve& sm) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    for (int r = warp; r < s.R; r += nwarps) {
+        float kh[S], kv[S];
+#pragma unroll
+        for (int k = 0; k < S; ++k) {
+            kh[k] = __ldg(s.kh + r * S + k);
+            kv[k] = __ldg(s.kv + r * S + k);
+        }
+        const int down = min(S, s.R - 1 - r);  // vertical offsets that stay in the frame
+        const float* row = sm.stage + r * s.RP;
+        for (int cs = 0; cs < s.W; cs += 32) {  // same trip count on every lane
+            const int c = cs + lane;
+            const float a = c < s.W ? row[c] : 0.0f;
+            const bool va = valid_range(a);
+            unsigned m = 0;
+            if (va) {
+#pragma unroll
+                for (int k = 1; k <= S; ++k) {
+                    const float b = row[c + k];
+                    if (valid_range(b) && edge_pred(a, b, kh[k - 1], s.delta2)) m |= 1u << (k - 1);
+                    if (k <= down) {
+                        const float d = row[c + k * s.RP];
+                        if (valid_range(d) && edge_pred(a, d, kv[k - 1], s.delta2))
+                            m |= 1u << (8 + k - 1);
+                    }
+                }
+            }
+            const unsigned vm = __ballot_sync(kFull, va);
+            if (c < s.W) sm.mask[(r << s.sh) + c] = (uint16_t)m;
+            if (lane == 0) sm.vmask[(r << (s.sh - 5)) + (cs >> 5)] = vm;
         }
     }
 }
@@ -293,36 +390,15 @@ __device__ void phase1_edges(const Strip& s, const Carve& sm, uint64_t* bar, uin
     __syncthreads();
 
     // 1. edge bits of every pixel, from shared memory
-    for (int r = warp; r < s.R; r += nwarps) {
-        float kh[kMaxSkip], kv[kMaxSkip];
-#pragma unroll
-        for (int k = 0; k < kMaxSkip; ++k) {
-            kh[k] = k < s.S ? __ldg(s.kh + r * s.S + k) : 0.0f;
-            kv[k] = k < s.S ? __ldg(s.kv + r * s.S + k) : 0.0f;
-        }
-        const float* row = sm.stage + r * s.RP;
-        for (int cs = 0; cs < s.W; cs += 32) {  // same trip count on every lane
-            const int c = cs + lane;
-            const float a = c < s.W ? row[c] : 0.0f;
-            const bool va = valid_range(a);
-            unsigned m = 0;
-            if (va) {
-#pragma unroll
-                for (int k = 1; k <= kMaxSkip; ++k) {
-                    if (k > s.S) break;
-                    const float b = row[c + k];
-                    if (valid_range(b) && edge_pred(a, b, kh[k - 1], s.delta2)) m |= 1u << (k - 1);
-                    if (r + k < s.R) {
-                        const float d = row[c + k * s.RP];
-                        if (valid_range(d) && edge_pred(a, d, kv[k - 1], s.delta2))
-                            m |= 1u << (8 + k - 1);
-                    }
-                }
-            }
-            const unsigned vm = __ballot_sync(kFull, va);
-            if (c < s.W) sm.mask[(r << s.sh) + c] = (uint16_t)m;
-            if (lane == 0) sm.vmask[(r << (s.sh - 5)) + (cs >> 5)] = vm;
-        }
+    switch (s.S) {
+        case 1: mask_rows<1>(s, sm); break;
+        case 2: mask_rows<2>(s, sm); break;
+        case 3: mask_rows<3>(s, sm); break;
+        case 4: mask_rows<4>(s, sm); break;
+        case 5: mask_rows<5>(s, sm); break;
+        case 6: mask_rows<6>(s, sm); break;
+        case 7: mask_rows<7>(s, sm); break;
+        default: mask_rows<8>(s, sm); break;
     }
     __syncthreads();
 }
@@ -366,153 +442,244 @@ __device__ void phase1_local(const Strip& s, const Carve& sm) {
         default: phase1_bands<8>(s, sm); break;
     }
     __syncthreads();
+    phase1_seams(s, sm);
+    __syncthreads();
 
-    // c. compress by pointer jumping: every round replaces each parent by its parent's
-    //    parent; each entry has exactly one writer (its owner thread), so a round never
-    //    stores a stale value over a newer one, and ceil(log2(depth)) rounds reach the roots
+    // c/d. every pixel's label: the global index of its strip-local root
     {
-        volatile int* vp = par;
-        const int n = s.R << s.sh;
-        int rounds = 0;
-        bool changed = true;
-        while (changed) {
-            bool any = false;
-            for (int i = threadIdx.x; i < n; i += blockDim.x) {
-                const int p = vp[i];
-                if (p >= 0) {
-                    const int gp = vp[p];
-                    if (gp != p) {
-                        vp[i] = gp;
-                        any = true;
+        const volatile int* vp = par;
+        const int lane = threadIdx.x & 31;
+        const int warp = threadIdx.x >> 5;
+        const int nwarps = blockDim.x >> 5;
+        const bool vec = ((s.C & 3) == 0) && ((s.c0 & 3) == 0) &&
+                         ((reinterpret_cast<uintptr_t>(s.labels) & 15) == 0);
+        for (int r = warp; r < s.R; r += nwarps) {
+            int32_t* out = s.labels + (size_t)r * s.C + s.c0;
+            const int base = r << s.sh;
+            for (int c = lane * 4; c < s.W; c += 128) {
+                int v[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    int p = c + q < s.W ? vp[base + c + q] : -1;
+                    if (p >= 0) {
+                        // read-only walk to the strip-local root (paths are short after the
+                        // band pass; nothing writes par any more)
+                        int budget = s.limit;
+                        p = find_smem_ro(vp, p, budget);
+                        if (budget <= 0) report_timeout(s.status);
+                        v[q] = global_of(s, p);
+                    } else {
+                        v[q] = -1;
                     }
                 }
+                if (vec && c + 4 <= s.W) {
+                    __stcg(reinterpret_cast<int4*>(out + c), make_int4(v[0], v[1], v[2], v[3]));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (c + q < s.W) __stcg(out + c + q, v[q]);
+                }
             }
-            changed = __syncthreads_or(any) != 0;
-            if (++rounds > 40) {  // depth < 2^16: 17 rounds suffice
-                if (threadIdx.x == 0) report_timeout(s.status);
-                break;
-            }
-        }
-    }
-
-    // d. publish the border pixels and border roots into the cross-strip forest
-    if (s.border) {
-        const int nb = s.S < s.W ? s.S : s.W;   // border columns on each side
-        const int per_row = 2 * nb;
-        for (int t = threadIdx.x; t < s.R * per_row; t += blockDim.x) {
-            const int r = t / per_row;
-            const int j = t - r * per_row;
-            const int c = j < nb ? j : s.W - per_row + j;  // first nb, then last nb columns
-            const int p = par[(r << s.sh) + c];
-            if (p < 0) continue;
-            const int groot = global_of(s, p);
-            if (j < nb) __stcg(s.labels + (size_t)r * s.C + s.c0 + c, groot);
-            __stcg(s.labels + groot, groot);
         }
     }
 }
 
-__device__ void phase2_merge(const Strip& s, const Carve& sm) {
-    if (!s.border) return;
-    const int first = s.W - s.S > 0 ? s.W - s.S : 0;
-    const int ncols = s.W - first;
-    const int n = s.R * ncols;
-    for (int t = threadIdx.x; t < n; t += blockDim.x) {
-        const int r = t / ncols;
-        const int c = first + (t - r * ncols);
-        const unsigned mk = sm.mask[(r << s.sh) + c];
-        for (int k = s.W - c; k <= s.S; ++k) {  // offsets that leave the strip
-            if (!((mk >> (k - 1)) & 1u)) continue;
-            int tc = s.c0 + c + k;
-            if (tc >= s.C) tc %= s.C;  // a set bit past the last column implies wrap
-            const int ga = global_of(s, sm.par[(r << s.sh) + c]);
-            const int gb = __ldcg(s.labels + (size_t)r * s.C + tc);
-            int budget = s.limit;
-            union_global(s.labels, ga, gb, budget);
-            if (budget <= 0) report_timeout(s.status);
-        }
-    }
-}
-
-__device__ void phase3_flatten(const Strip& s, int* par) {
-    if (s.border) {
-        // roots of border components: global root, stored as the tag -(root + 2)
-        const int nb = s.S < s.W ? s.S : s.W;
-        const int per_row = 2 * nb;
-        for (int t = threadIdx.x; t < s.R * per_row; t += blockDim.x) {
-            const int r = t / per_row;
-            const int j = t - r * per_row;
-            const int c = j < nb ? j : s.W - per_row + j;
-            const int p = par[(r << s.sh) + c];
-            if (p < 0) continue;  // not a measurement, or a root already tagged
-            const int groot = global_of(s, p);
-            int budget = s.limit;
-            const int fin = find_global(s.labels, groot, budget, false);
-            if (budget <= 0) report_timeout(s.status);
-            if (fin != groot) par[p] = -(fin + 2);
-        }
-        __syncthreads();
-    }
-    // every pixel of the strip: 4 consecutive columns per thread
+// P2: the boundary merge of one border (strip b's right edge, to strip b + 1 or across
+// the seam to strip 0), by the block that completes the second of its two strips.  Lanes
+// are rows; each lane loads its row's S readings and labels on both sides of the border
+// at once, tests the crossing edges, and of consecutive rows that would unite the same
+// pair of strip-local roots only the first asks.
+template <int S>
+__device__ void border_merge_s(const FrameDesc& f, int b, int limit) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    const bool vec = ((s.C & 3) == 0) && ((s.c0 & 3) == 0) &&
-                     ((reinterpret_cast<uintptr_t>(s.labels) & 15) == 0);
-    for (int r = warp; r < s.R; r += nwarps) {
-        int32_t* out = s.labels + (size_t)r * s.C + s.c0;
-        const int base = r << s.sh;
-        for (int c = lane * 4; c < s.W; c += 128) {
-            int v[4];
+    const int R = f.rows, C = f.cols;
+    const int c0 = b * f.strip_w;
+    const int W = min(f.strip_w, C - c0);  // >= S (several strips, or C >= S)
+    const int first = W - S;
+    const int rblocks = (R + 31) >> 5;
+    for (int rb = warp; rb < rblocks; rb += nwarps) {
+        const int r = (rb << 5) + lane;
+        const bool row_ok = r < R;
+        const float* rrow = f.range + (size_t)(row_ok ? r : 0) * C;
+        const int32_t* lrow = f.labels + (size_t)(row_ok ? r : 0) * C;
+        float av[S], dv[S], kh[S];
+        int la[S], lb[S];
+        int done_a = -1, done_b = -1;  // the last pair this lane united
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                int x = -1;
-                if (c + q < s.W) {
-                    const int p = par[base + c + q];
-                    if (p <= -2) {
-                        x = -(p + 2);
-                    } else if (p >= 0) {
-                        const int w = par[p];
-                        x = w <= -2 ? -(w + 2) : global_of(s, p);
-                    }
+        for (int j = 0; j < S; ++j) {
+            int tc = c0 + W + j;  // j-th column past the border
+            if (tc >= C && f.wrap) tc %= C;
+            const bool tok = row_ok && tc < C;
+            av[j] = row_ok ? load_range(rrow + c0 + first + j) : 0.0f;
+            la[j] = row_ok ? __ldcg(lrow + c0 + first + j) : 0;
+            dv[j] = tok ? load_range(rrow + tc) : 0.0f;
+            lb[j] = tok ? __ldcg(lrow + tc) : 0;
+            kh[j] = __ldg(f.kh + (row_ok ? r : 0) * S + j);
+        }
+#pragma unroll
+        for (int j = 0; j < S; ++j) {            // source column first + j
+#pragma unroll
+            for (int k = S - j; k <= S; ++k) {   // offsets that cross: target j + k - S
+                const int t = j + k - S;
+                const bool e = av[j] > 0.0f && dv[t] > 0.0f && edge_pred(av[j], dv[t], kh[k - 1], f.delta2);
+                const int ga = la[j], gb = lb[t];
+                const int pa = __shfl_up_sync(kFull, ga, 1);
+                const int pb = __shfl_up_sync(kFull, gb, 1);
+                const unsigned em = __ballot_sync(kFull, e);
+                // dropped when the row above asks for the same pair, or when this row
+                // already asked for it at another column or offset
+                const bool dup = (lane > 0 && ((em >> (lane - 1)) & 1u) && pa == ga && pb == gb) ||
+                                 (ga == done_a && gb == done_b);
+                if (e && !dup && ga != gb) {
+                    int budget = limit;
+                    union_global(f.labels, ga, gb, budget);
+                    if (budget <= 0) report_timeout(f.status);
+                    done_a = ga;
+                    done_b = gb;
                 }
-                v[q] = x;
-            }
-            if (vec && c + 4 <= s.W) {
-                __stcs(reinterpret_cast<int4*>(out + c), make_int4(v[0], v[1], v[2], v[3]));
-            } else {
-#pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (c + q < s.W) out[c + q] = v[q];
             }
         }
     }
 }
 
-__global__ void __launch_bounds__(1024) flic_label_kernel(const LabelLaunch L) {
+// The same for a single strip narrower than S (wrapping onto itself): plain loops.
+__device__ void border_merge_narrow(const FrameDesc& f, int limit) {
+    const int R = f.rows, C = f.cols, S = f.skip;
+    for (int t = threadIdx.x; t < R * C; t += blockDim.x) {
+        const int r = t / C, c = t - r * C;
+        const float a = load_range(f.range + t);
+        if (!(a > 0.0f)) continue;
+        for (int k = C - c; k <= S; ++k) {
+            const int tc = (c + k) % C;
+            const float d = load_range(f.range + (size_t)r * C + tc);
+            if (d > 0.0f && edge_pred(a, d, __ldg(f.kh + r * S + k - 1), f.delta2)) {
+                int budget = limit;
+                union_global(f.labels, __ldcg(f.labels + t), __ldcg(f.labels + (size_t)r * C + tc),
+                             budget);
+                if (budget <= 0) report_timeout(f.status);
+            }
+        }
+    }
+}
+
+__device__ void border_merge(const FrameDesc& f, int b) {
+    const int limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
+    const int W = min(f.strip_w, f.cols - b * f.strip_w);
+    if (W < f.skip) {
+        border_merge_narrow(f, limit);
+        return;
+    }
+    switch (f.skip) {
+        case 1: border_merge_s<1>(f, b, limit); break;
+        case 2: border_merge_s<2>(f, b, limit); break;
+        case 3: border_merge_s<3>(f, b, limit); break;
+        case 4: border_merge_s<4>(f, b, limit); break;
+        case 5: border_merge_s<5>(f, b, limit); break;
+        case 6: border_merge_s<6>(f, b, limit); break;
+        case 7: border_merge_s<7>(f, b, limit); break;
+        default: border_merge_s<8>(f, b, limit); break;
+    }
+}
+
+// P3: flatten one strip once its frame's forest is final.  Consecutive pixels usually
+// share a strip-local root, so each thread remembers its last lookup.
+__device__ void phase3_strip(const FrameDesc& f, int si) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int c0 = si * f.strip_w;
+    const int W = min(f.strip_w, f.cols - c0);
+    const int limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
+    const bool vec = ((f.cols & 3) == 0) && ((c0 & 3) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(f.labels) & 15) == 0);
+    int last_l = -1, last_root = -1;
+    for (int r = warp; r < f.rows; r += nwarps) {
+        int32_t* row = f.labels + (size_t)r * f.cols + c0;
+        for (int c = lane * 4; c < W; c += 128) {
+            int v[4];
+            const bool full = vec && c + 4 <= W;
+            if (full) {
+                const int4 x = __ldcg(reinterpret_cast<const int4*>(row + c));
+                v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q) v[q] = c + q < W ? __ldcg(row + c + q) : -1;
+            }
+            bool changed = false;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int l = v[q];
+                if (l < 0) continue;
+                if (l != last_l) {
+                    int budget = limit;
+                    last_root = find_global(f.labels, l, budget, false);
+                    if (budget <= 0) report_timeout(f.status);
+                    last_l = l;
+                }
+                if (last_root != l) {
+                    v[q] = last_root;
+                    changed = true;
+                }
+            }
+            if (changed) {
+                if (full) {
+                    __stcg(reinterpret_cast<int4*>(row + c), make_int4(v[0], v[1], v[2], v[3]));
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (c + q < W) __stcg(row + c + q, v[q]);
+                }
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t tma_bar;
+    __shared__ int task_sh;
+    __shared__ int flag_sh;
     if (threadIdx.x == 0) mbar_init(&tma_bar, 1);
     __syncthreads();
     uint32_t parity = 0;
 
-    const unsigned rank = cluster_ctarank();
-    const int nitems = L.items ? L.nitems : 1;
-    // every block of a cluster walks the same item sequence, so the cluster barriers
-    // below are reached the same number of times by all of them
-    for (int item = (int)cluster_index(); item < nitems; item += (int)cluster_count()) {
-        int fi, si;
-        if (L.items) {
-            fi = L.items[item].frame[rank];
-            si = L.items[item].strip[rank];
-        } else {
-            fi = (int)rank < L.single.nstrips ? 0 : -1;
-            si = (int)rank;
+    while (true) {
+        if (threadIdx.x == 0) task_sh = atomicAdd(L.counters + kCtrNext, 1);
+        __syncthreads();
+        const int t = task_sh;
+        __syncthreads();  // task_sh is rewritten by the next iteration
+        if (t >= L.ntasks) break;
+
+        int fi, si, kind;
+        if (L.tasks) {
+            const Task tk = L.tasks[t];
+            fi = tk.frame;
+            si = tk.strip;
+            kind = tk.kind;
+        } else {  // one frame: P1 of strips 0..n-1, then P3 of strips 0..n-1
+            fi = 0;
+            si = t < L.single.nstrips ? t : t - L.single.nstrips;
+            kind = t < L.single.nstrips ? kTaskP1 : kTaskP3;
         }
-        Strip s{};
-        const bool active = fi >= 0;
-        if (active) {
-            const FrameDesc& f = L.frames ? L.frames[fi] : L.single;
+        const FrameDesc f = L.frames ? L.frames[fi] : L.single;
+        const bool border = f.nstrips > 1 || f.wrap;
+        // [borders merged, ready, arrivals at border 0, 1, ...]
+        int* done_ctr = L.counters + kCtrFrames + kCtrPerFrame * fi;
+
+        if (kind == kTaskP1) {
+            Strip s{};
             s.range = f.range;
             s.labels = f.labels;
             s.kv = f.kv;
@@ -523,7 +690,7 @@ __global__ void __launch_bounds__(1024) flic_label_kernel(const LabelLaunch L) {
             s.S = f.skip;
             s.delta2 = f.delta2;
             s.wrap = f.wrap != 0;
-            s.border = f.nstrips > 1 || s.wrap;
+            s.border = border;
             s.c0 = si * f.strip_w;
             s.W = min(f.strip_w, s.C - s.c0);
             s.sh = f.pitch_log2;
@@ -531,21 +698,63 @@ __global__ void __launch_bounds__(1024) flic_label_kernel(const LabelLaunch L) {
             s.bulk = ((s.C & 3) == 0) && ((s.c0 & 3) == 0) && ((s.W & 3) == 0) &&
                      ((reinterpret_cast<uintptr_t>(s.range) & 15) == 0);
             s.limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
-        }
-        const Carve sm = carve(smem_raw, s);
-
-        if (active) {
+            const Carve sm = carve(smem_raw, s);
             phase1_edges(s, sm, &tma_bar, parity);
             if (s.bulk) parity ^= 1u;
             phase1_local(s, sm);
+            if (border) {
+                // arrive at the (up to two) borders of this strip; the second arrival at a
+                // border merges it, and the last merged border makes the frame ready
+                const int n = f.nstrips;
+                const int nb = f.wrap ? n : n - 1;
+                __threadfence();
+                __syncthreads();
+                for (int side = 0; side < 2; ++side) {
+                    const int b = side == 0 ? si : si - 1;  // right border, then left border
+                    const int bb = b < 0 ? (f.wrap ? n - 1 : -1) : b;
+                    if (bb < 0 || bb >= nb || (side == 1 && n == 1)) continue;  // uniform
+                    if (threadIdx.x == 0) {
+                        const int need = n == 1 ? 1 : 2;
+                        flag_sh = atomicAdd(done_ctr + 2 + bb, 1) == need - 1;
+                    }
+                    __syncthreads();
+                    if (flag_sh) {
+                        __threadfence();
+                        border_merge(f, bb);
+                        __threadfence();
+                        __syncthreads();
+                        if (threadIdx.x == 0 && atomicAdd(done_ctr, 1) == nb - 1)
+                            st_release(done_ctr + 1, 1);
+                    }
+                    __syncthreads();
+                }
+            }
+        } else {
+            if (threadIdx.x == 0) {
+                int it = 0;
+                flag_sh = 1;
+                while (ld_acquire(done_ctr + 1) == 0) {
+                    __nanosleep(128);
+                    if (++it > (1 << 24)) {  // ~2 s: give up and leave the strip alone,
+                        report_timeout(f.status);  // its labels may not be written yet
+                        flag_sh = 0;
+                        break;
+                    }
+                }
+            }
+            __syncthreads();
+            if (flag_sh) phase3_strip(f, si);
         }
+        __syncthreads();  // shared memory is reused by the next task
+    }
+
+    // the last block to leave resets the counters for the next launch on this stream
+    if (threadIdx.x == 0) {
         __threadfence();
-        cluster_barrier();
-        if (active) phase2_merge(s, sm);
-        __threadfence();
-        cluster_barrier();
-        if (active) phase3_flatten(s, sm.par);
-        __syncthreads();  // shared memory is reused by the next item
+        if (atomicAdd(L.counters + kCtrExit, 1) == (int)gridDim.x - 1) {
+            for (size_t i = 0; i < counter_ints(L.nframes); ++i) L.counters[i] = 0;
+            __threadfence();
+        }
     }
 }
 
@@ -583,44 +792,18 @@ __global__ void flic_edges_kernel(const FrameDesc f, uint16_t* __restrict__ mask
 }  // namespace
 
 cudaError_t label_kernel_setup(size_t max_smem) {
-    cudaError_t e = cudaFuncSetAttribute(flic_label_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)max_smem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(flic_label_kernel,
-                                cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    return cudaFuncSetAttribute(flic_label_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)max_smem);
 }
 
-cudaError_t launch_label(const LabelLaunch& L, int grid_clusters, int threads, size_t smem,
+cudaError_t launch_label(const LabelLaunch& L, int grid, int threads, size_t smem,
                          cudaStream_t stream) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(grid_clusters * L.cluster), 1, 1);
-    cfg.blockDim = dim3((unsigned)threads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cfg.stream = stream;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)L.cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, flic_label_kernel, L);
+    flic_label_kernel<<<grid, threads, smem, stream>>>(L);
+    return cudaGetLastError();
 }
 
-cudaError_t max_active_clusters(int cluster, int threads, size_t smem, int* out) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)cluster, 1, 1);
-    cfg.blockDim = dim3((unsigned)threads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = (unsigned)cluster;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    return cudaOccupancyMaxActiveClusters(out, flic_label_kernel, &cfg);
+cudaError_t label_blocks_per_sm(int threads, size_t smem, int* out) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, flic_label_kernel, threads, smem);
 }
 
 cudaError_t launch_edges(const FrameDesc& f, uint16_t* mask, cudaStream_t stream) {

@@ -24,7 +24,7 @@ FLIC_ERR_TIMEOUT = 4
 FLIC_ERR_BUSY = 5
 FLIC_ERR_UNSUPPORTED = 6
 FLIC_FLAG_NO_WRAP = 1
-FLIC_MAX_PIXELS = 1 << 19
+FLIC_MAX_PIXELS = 1 << 21
 FLIC_MAX_ROWS = 512
 FLIC_MAX_SKIP = 8
 FLIC_NOALLOC_MAX_PIXELS = 1 << 18
@@ -173,15 +173,15 @@ def flic_plan_info(h: Handle) -> dict:
 
 
 def flic_plan_frame(rows: int, cols: int, skip: int, px_per_cta: int = 16384,
-                    max_cluster: int = 16) -> dict:
+                    max_strips: int = 64) -> dict:
     """Host-only strip split (no GPU needed)."""
     info = np.zeros(4, np.int32)
-    _check(_lib.flic_plan_frame(rows, cols, skip, px_per_cta, max_cluster, info.ctypes.data))
+    _check(_lib.flic_plan_frame(rows, cols, skip, px_per_cta, max_strips, info.ctypes.data))
     return dict(strips=int(info[0]), strip_w=int(info[1]), pitch=int(info[2]), smem=int(info[3]))
 
 
-def flic_set_tuning(h: Handle, px_per_cta: int = 0, threads: int = 0, cluster: int = 0) -> None:
-    _check(_lib.flic_set_tuning(h.ptr, px_per_cta, threads, cluster))
+def flic_set_tuning(h: Handle, px_per_cta: int = 0, threads: int = 0, max_strips: int = 0) -> None:
+    _check(_lib.flic_set_tuning(h.ptr, px_per_cta, threads, max_strips))
 
 
 def flic_edges(h: Handle, range_img, mask, stream=None) -> None:
@@ -242,17 +242,17 @@ def flic_batch_destroy(b: Batch) -> None:
     b.close()
 
 
-def flic_batch_set_tuning(b: Batch, px_per_cta: int = 0, threads: int = 0, cluster: int = 0,
+def flic_batch_set_tuning(b: Batch, px_per_cta: int = 0, threads: int = 0, max_strips: int = 0,
                           ctas_per_sm: int = 0) -> None:
-    _check(_lib.flic_batch_set_tuning(b.ptr, px_per_cta, threads, cluster, ctas_per_sm))
+    _check(_lib.flic_batch_set_tuning(b.ptr, px_per_cta, threads, max_strips, ctas_per_sm))
 
 
 def flic_batch_last_plan(b: Batch) -> dict:
     info = np.zeros(8, np.int32)
     _check(_lib.flic_batch_last_plan(b.ptr, info.ctypes.data))
-    return dict(items=int(info[0]), grid_clusters=int(info[1]), cluster=int(info[2]),
+    return dict(tasks=int(info[0]), grid=int(info[1]), max_strips=int(info[2]),
                 threads=int(info[3]), smem=int(info[4]), strips=int(info[5]),
-                frames=int(info[6]))
+                frames=int(info[6]), resident_blocks=int(info[7]))
 
 
 class BatchArgs:

@@ -78,10 +78,10 @@ def test_strip_planner_invariants(lib_path, seed):
     from paper_2003_00575_gb300 import flic
     g = np.random.default_rng(seed)
     R = int(g.integers(1, 513))
-    C = int(g.integers(1, max(2, (1 << 19) // R + 1)))
+    C = int(g.integers(1, max(2, (1 << 21) // R + 1)))
     S = int(g.integers(1, 9))
-    px = int(g.choice([64, 1024, 4096, 16384, 32768]))
-    cl = int(g.integers(1, 17))
+    px = int(g.choice([64, 1024, 4096, 8192, 16384, 32768]))
+    cl = int(g.integers(1, 65))
     try:
         p = flic.flic_plan_frame(R, C, S, px, cl)
     except flic.FlicError as e:

@@ -116,8 +116,8 @@ def test_hand_example_on_gpu(flic, golden_dir):
         np.testing.assert_array_equal(got, np.array(case["labels"]), err_msg=str(case))
 
 
-TUNINGS = [(0, 0, 0), (64, 128, 16), (256, 256, 4), (1024, 1024, 8), (4096, 512, 4),
-           (32768, 256, 4), (512, 128, 16), (8192, 1024, 12)]
+TUNINGS = [(0, 0, 0), (64, 128, 64), (256, 256, 4), (1024, 512, 8), (4096, 512, 4),
+           (32768, 256, 4), (512, 128, 16), (8192, 512, 12), (2048, 256, 64)]
 
 
 @pytest.mark.parametrize("tuning", TUNINGS)
@@ -150,7 +150,7 @@ def _random_frame(seed):
     elev = np.radians(np.linspace(10, -10, R)) if R > 1 else np.array([0.0])
     az = 2 * math.pi / C
     delta = float(np.float32(g.uniform(0.1, 1.5)))
-    tuning = [(0, 0, 0), (64, 128, 16), (128, 256, 8), (1024, 512, 3)][int(g.integers(0, 4))]
+    tuning = [(0, 0, 0), (64, 128, 64), (128, 256, 8), (1024, 512, 3)][int(g.integers(0, 4))]
     return rng.astype(np.float32), elev, az, delta, S, wrap, tuning
 
 
@@ -180,7 +180,7 @@ DEGENERATE = {
 
 
 @pytest.mark.parametrize("name", list(DEGENERATE))
-@pytest.mark.parametrize("skip,wrap,tuning", [(1, True, (0, 0, 0)), (5, True, (64, 128, 16)),
+@pytest.mark.parametrize("skip,wrap,tuning", [(1, True, (0, 0, 0)), (5, True, (64, 128, 64)),
                                               (8, False, (128, 256, 4)), (3, False, (0, 0, 0))])
 def test_labels_degenerate(flic, name, skip, wrap, tuning):
     rng = DEGENERATE[name].astype(np.float32)
@@ -192,9 +192,9 @@ def test_labels_degenerate(flic, name, skip, wrap, tuning):
     np.testing.assert_array_equal(got, want)
 
 
-@pytest.mark.parametrize("shape", [(128, 4096), (512, 1024), (16, 32768)])
+@pytest.mark.parametrize("shape", [(128, 4096), (512, 1024), (16, 32768), (256, 8192)])
 def test_largest_frames(flic, shape):
-    """Frames at the documented pixel limit (2^19), split over 16 strips."""
+    """Large frames up to the documented pixel limit (2^21), split over up to 64 strips."""
     R, C = shape
     g = np.random.default_rng(R)
     base = 20 + 5 * np.sin(np.arange(C) / 50.0)[None, :] + 0.01 * np.arange(R)[:, None]
@@ -209,7 +209,7 @@ def test_largest_frames(flic, shape):
 
 def test_oversized_frame_rejected(flic):
     with pytest.raises(flic.FlicError) as e:
-        flic.flic_create(512, 2048, np.zeros(512), 2 * math.pi / 2048, 0.5, 1)
+        flic.flic_create(512, 8192, np.zeros(512), 2 * math.pi / 8192, 0.5, 1)
     assert e.value.status == flic.FLIC_ERR_INVALID
 
 
@@ -344,8 +344,8 @@ def test_batch_full_c4_matches_oracle(flic, c4_frames, c4_oracle):
     assert not bad, (plan, bad[:20], len(bad))
 
 
-@pytest.mark.parametrize("tuning", [(4096, 256, 8, 0), (16384, 512, 16, 1), (32768, 1024, 8, 0),
-                                    (2048, 128, 16, 2)])
+@pytest.mark.parametrize("tuning", [(4096, 256, 64, 0), (16384, 512, 16, 1), (32768, 512, 8, 0),
+                                    (2048, 128, 64, 2), (8192, 256, 64, 1)])
 def test_batch_shapes_and_tunings(flic, c4_frames, c4_oracle, tuning):
     idx = list(range(0, 256, 7))
     got, _ = _run_batch(flic, [c4_frames[i] for i in idx], tuning=tuning)

@@ -243,6 +243,64 @@ flic_status flic_device_status(flic_handle h, int32_t clear);
 flic_status flic_debug_set_iter_limit(flic_handle h, int32_t limit);
 
 /*
+ * Serving (no counterpart in the paper, which processes one recorded frame at a time):
+ * a request loop for several sensors that admits frames as device memory frees up,
+ * batches whatever has arrived into one labelling launch, and overlaps batches on
+ * several streams (continuous batching).  Results equal the single-frame calls.
+ *
+ * flic_server_create — a server for nsensors sensors:
+ *   sensors         host array of handles; each slot gets its own copy of the sensor's
+ *                   tables and scratch, so the caller may destroy these afterwards
+ *   max_points      host array: largest cloud per sensor (0: range images only)
+ *   nstreams        CUDA streams batches rotate over (1..8; 2 overlaps one batch's
+ *                   copies and kernels with the next)
+ *   max_batch       frames per launch (1..4096)
+ *   mem_budget      device bytes for frame slots (each slot holds one in-flight frame:
+ *                   range image, labels, xyz, pixel map, point labels); at least one slot
+ *                   per sensor is created
+ *   max_queue       requests that may wait for a slot before submit refuses (>= 1)
+ *   Starts one dispatcher thread.  Errors: INVALID, OOM, CUDA.
+ * flic_server_submit — queue one frame; returns at once:
+ *   sensor, kind    sensor index; kind 0 = range image (host_in: rows*cols fp32),
+ *                   kind 1 = point cloud (host_in: n*3 fp32 xyz, n <= max_points)
+ *   host_out        labels, written when the frame completes: rows*cols int32 (kind 0)
+ *                   or n int32 point labels (kind 1)
+ *   Both host buffers must stay valid until the frame's completion is polled; pinned
+ *   (page-locked) buffers keep the copies asynchronous.  FLIC_ERR_BUSY when max_queue
+ *   requests are already waiting (counted as rejected).
+ * flic_server_poll — move up to max completion records to out (non-blocking); returns
+ *   the number moved.
+ * flic_server_drain — wait until every submitted frame has completed (or timeout_s).
+ * flic_server_stats — out, host, 8 int64: submitted, rejected, completed, batches,
+ *   largest batch, slots, device bytes of the slots, batches in flight now.
+ * flic_server_destroy — drains, stops the dispatcher, frees everything.
+ */
+typedef struct flic_server_ctx* flic_server;
+typedef struct {
+    uint64_t tag;        /* caller's tag from flic_server_submit */
+    int32_t sensor;
+    int32_t kind;
+    int64_t n;           /* points (kind 1) or pixels (kind 0) */
+    int32_t status;      /* FLIC_OK, or the error of the launch that carried the frame */
+    int32_t batch_size;  /* frames in the launch that carried it */
+    double t_submit;     /* seconds on the server's monotonic clock */
+    double t_launch;     /* its batch was enqueued */
+    double t_done;       /* its results were in host memory */
+} flic_completion;
+
+flic_status flic_server_create(const flic_handle* sensors, int32_t nsensors,
+                               const int64_t* max_points, int32_t nstreams, int32_t max_batch,
+                               int64_t mem_budget, int32_t max_queue, flic_server* out);
+flic_status flic_server_submit(flic_server s, int32_t sensor, int32_t kind, const void* host_in,
+                               int64_t n, int32_t* host_out, uint64_t tag);
+int32_t flic_server_poll(flic_server s, flic_completion* out, int32_t max);
+flic_status flic_server_drain(flic_server s, double timeout_s);
+flic_status flic_server_stats(flic_server s, int64_t* out);
+flic_status flic_server_destroy(flic_server s);
+/* The server's monotonic clock in seconds (the clock of the completion records). */
+double flic_server_clock(void);
+
+/*
  * flic_project_noalloc — flic_project for callers that cannot allocate device memory
  * (the paper has no counterpart; this is an integration entry point).  Some callers may
  * only use the buffers they are handed: code running inside a host framework whose

@@ -128,6 +128,7 @@ struct flic_ctx {
     float* d_kv = nullptr;
     float* d_kh = nullptr;
     std::vector<float> h_kv, h_kh;
+    std::vector<double> elev;  // the creation arguments, for flic::clone_handle
     bool proj_ok = false;
     float* d_colb = nullptr;
     float* d_rowb = nullptr;
@@ -154,12 +155,14 @@ struct flic_batch_ctx {
     flic::FrameDesc* d_frames = nullptr;
     flic::Task* d_tasks = nullptr;
     int32_t* d_counters = nullptr;
+    int32_t* h_dims = nullptr;  // pinned [ntasks, nframes]
+    int32_t* d_dims = nullptr;
     cudaEvent_t staged = nullptr;       // descriptor upload done: staging reusable
     cudaEvent_t kernel_done = nullptr;  // last launch done: device descriptors reusable
     bool pending = false;
     cudaStream_t cap_stream = nullptr;
     Tuning tune;
-    std::map<std::tuple<int, int, int, int, size_t>, cudaGraphExec_t> graphs;  // ntasks, nframes, grid, threads, smem
+    std::map<std::tuple<int, int, size_t>, cudaGraphExec_t> graphs;  // grid, threads, smem
     int last_info[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // the previous call's arguments and launch shape: an identical call replays the graph
     std::vector<const void*> last_args;
@@ -320,6 +323,7 @@ flic_status flic_create_ex(int32_t rows, int32_t cols, const double* elevation, 
     h->wrap = (flags & FLIC_FLAG_NO_WRAP) ? 0 : 1;
     h->az_step = az_step;
     h->uid = g_next_uid.fetch_add(1);
+    h->elev.assign(elevation, elevation + rows);
     cudaGetDevice(&h->device);
 
     flic_status st;
@@ -528,6 +532,8 @@ flic_status flic_batch_create(int32_t max_frames, flic_batch* out) {
         (e = cudaMalloc((void**)&b->d_tasks, tb)) != cudaSuccess ||
         (e = cudaMalloc((void**)&b->d_counters, cb)) != cudaSuccess ||
         (e = cudaMemset(b->d_counters, 0, cb)) != cudaSuccess ||
+        (e = cudaHostAlloc((void**)&b->h_dims, 2 * sizeof(int32_t), cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&b->d_dims, 2 * sizeof(int32_t))) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->kernel_done, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
@@ -555,6 +561,8 @@ flic_status flic_batch_destroy(flic_batch b) {
     clear_graphs(b);
     if (b->h_frames) cudaFreeHost(b->h_frames);
     if (b->h_tasks) cudaFreeHost(b->h_tasks);
+    if (b->h_dims) cudaFreeHost(b->h_dims);
+    cudaFree(b->d_dims);
     cudaFree(b->d_frames);
     cudaFree(b->d_tasks);
     cudaFree(b->d_counters);
@@ -675,7 +683,11 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
     }
     while (next_pending < pending.size()) emit_p3(pending[next_pending++].second);
     const int ntasks = nt;
-    const int grid = std::min(ntasks, resident);
+    // the whole resident grid every time (idle blocks leave at once), so the captured
+    // launch depends only on the block shape and can be replayed for any batch
+    const int grid = resident;
+    b->h_dims[0] = ntasks;
+    b->h_dims[1] = nframes;
 
     // descriptors: the previous kernel (on whatever stream) must be done reading them
     if (b->pending) {
@@ -687,12 +699,14 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_tasks, b->h_tasks, sizeof(flic::Task) * ntasks,
                             cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_dims, b->h_dims, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaEventRecord(b->staged, st);
     if (e != cudaSuccess) return cuda_fail(e, "descriptor upload");
     b->pending = true;
 
     // the persistent kernel, captured once per launch shape and replayed
-    auto key = std::make_tuple(ntasks, nframes, grid, t.threads, smem);
+    auto key = std::make_tuple(grid, t.threads, smem);
     auto found = b->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     if (found != b->graphs.end()) {
@@ -704,8 +718,7 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
         flic::LabelLaunch L{};
         L.frames = b->d_frames;
         L.tasks = b->d_tasks;
-        L.ntasks = ntasks;
-        L.nframes = nframes;
+        L.dims = b->d_dims;
         L.counters = b->d_counters;
         cudaError_t le = flic::launch_label(L, grid, t.threads, smem, b->cap_stream);
         e = cudaStreamEndCapture(b->cap_stream, &graph);
@@ -732,3 +745,16 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
 }
 
 }  // extern "C"
+
+flic_status flic::clone_handle(flic_handle h, flic_handle* out, int* rows, int* cols) {
+    if (!h) return fail(FLIC_ERR_INVALID, "NULL handle");
+    *rows = h->R;
+    *cols = h->C;
+    flic_status st = flic_create_ex(h->R, h->C, h->elev.data(), h->az_step, h->delta, h->S,
+                                    h->flags, out);
+    if (st == FLIC_OK) {
+        (*out)->tune = h->tune;
+        replan(*out);
+    }
+    return st;
+}

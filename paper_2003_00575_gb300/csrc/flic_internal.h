@@ -56,8 +56,9 @@ __host__ __device__ inline size_t counter_ints(int nframes) {
 struct LabelLaunch {
     const FrameDesc* frames;   // device array (batch), or nullptr: use `single`
     const Task* tasks;         // device array (batch), or nullptr: implicit single-frame queue
-    int32_t ntasks;
+    int32_t ntasks;            // used when dims == nullptr
     int32_t nframes;
+    const int32_t* dims;       // device [ntasks, nframes] (batch: uploaded with the tasks)
     int32_t* counters;         // counter_ints(nframes), zero at launch
     FrameDesc single;
 };
@@ -100,6 +101,12 @@ cudaError_t launch_decode(const ProjDesc& P, const unsigned long long* keys, flo
                           cudaStream_t stream);
 // Sets the thread-local message returned by flic_last_error().
 void set_last_error(const char* msg);
+
+}  // namespace flic
+#include "flic.h"
+namespace flic {
+// A new handle with the same geometry, threshold, skip, flags and tuning as h.
+flic_status clone_handle(flic_handle h, flic_handle* out, int* rows, int* cols);
 
 cudaError_t launch_scatter(const int32_t* labels, int64_t npix, const int32_t* point_pixel,
                            int64_t n, int32_t* point_labels, cudaStream_t stream);

@@ -654,13 +654,15 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
     if (threadIdx.x == 0) mbar_init(&tma_bar, 1);
     __syncthreads();
     uint32_t parity = 0;
+    const int ntasks = L.dims ? L.dims[0] : L.ntasks;
+    const int nframes = L.dims ? L.dims[1] : L.nframes;
 
     while (true) {
         if (threadIdx.x == 0) task_sh = atomicAdd(L.counters + kCtrNext, 1);
         __syncthreads();
         const int t = task_sh;
         __syncthreads();  // task_sh is rewritten by the next iteration
-        if (t >= L.ntasks) break;
+        if (t >= ntasks) break;
 
         int fi, si, kind;
         if (L.tasks) {
@@ -752,7 +754,7 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
     if (threadIdx.x == 0) {
         __threadfence();
         if (atomicAdd(L.counters + kCtrExit, 1) == (int)gridDim.x - 1) {
-            for (size_t i = 0; i < counter_ints(L.nframes); ++i) L.counters[i] = 0;
+            for (size_t i = 0; i < counter_ints(nframes); ++i) L.counters[i] = 0;
             __threadfence();
         }
     }

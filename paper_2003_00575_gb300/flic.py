@@ -60,6 +60,13 @@ SIGNATURES = {
     "flic_device_status": (_I32, [_P, _I32]),
     "flic_debug_set_iter_limit": (_I32, [_P, _I32]),
     "flic_project_noalloc": (_I32, [_I32, _I32, _P, _F64, _P, _I64, _P, _P, _P]),
+    "flic_server_create": (_I32, [_P, _I32, _P, _I32, _I32, _I64, _I32, _P]),
+    "flic_server_submit": (_I32, [_P, _I32, _I32, _P, _I64, _P, ctypes.c_uint64]),
+    "flic_server_poll": (_I32, [_P, _P, _I32]),
+    "flic_server_drain": (_I32, [_P, _F64]),
+    "flic_server_stats": (_I32, [_P, _P]),
+    "flic_server_destroy": (_I32, [_P]),
+    "flic_server_clock": (_F64, []),
 }
 
 
@@ -297,3 +304,75 @@ def flic_project_noalloc(rows: int, cols: int, elevation, az_step: float, xyz, r
                                      _dptr(range_out, "float32", rows * cols, "range_out"),
                                      _dptr(point_pixel, "int32", n, "point_pixel"),
                                      _stream(stream)))
+
+
+class flic_completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("sensor", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("n", ctypes.c_int64), ("status", ctypes.c_int32), ("batch_size", ctypes.c_int32),
+                ("t_submit", ctypes.c_double), ("t_launch", ctypes.c_double),
+                ("t_done", ctypes.c_double)]
+
+
+class Server:
+    def __init__(self, ptr: int):
+        self.ptr = ptr
+
+    def close(self) -> None:
+        if self.ptr:
+            _check(_lib.flic_server_destroy(self.ptr))
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            if self.ptr:
+                _lib.flic_server_destroy(self.ptr)
+        except Exception:
+            pass
+
+
+def flic_server_create(sensors, max_points, nstreams: int = 2, max_batch: int = 256,
+                       mem_budget: int = 1 << 30, max_queue: int = 4096) -> Server:
+    n = len(sensors)
+    hs = (ctypes.c_void_p * n)(*[h.ptr for h in sensors])
+    mp = (ctypes.c_int64 * n)(*[int(x) for x in max_points])
+    out = ctypes.c_void_p()
+    _check(_lib.flic_server_create(hs, n, mp, nstreams, max_batch, int(mem_budget), max_queue,
+                                   ctypes.byref(out)))
+    return Server(out.value)
+
+
+def flic_server_submit(srv: Server, sensor: int, kind: int, host_in, host_out, tag: int) -> int:
+    """host_in/host_out: pinned CPU tensors (float32 input, int32 output).  Returns the
+    status (FLIC_OK or FLIC_ERR_BUSY when the admission queue is full)."""
+    n = host_in.numel() // 3 if kind == 1 else host_in.numel()
+    st = _lib.flic_server_submit(srv.ptr, sensor, kind, host_in.data_ptr(), n,
+                                 host_out.data_ptr(), tag)
+    if st not in (FLIC_OK, FLIC_ERR_BUSY):
+        _check(st)
+    return st
+
+
+def flic_server_poll(srv: Server, max_records: int = 4096):
+    buf = (flic_completion * max_records)()
+    k = _lib.flic_server_poll(srv.ptr, buf, max_records)
+    return [buf[i] for i in range(k)]
+
+
+def flic_server_drain(srv: Server, timeout_s: float = 30.0) -> None:
+    _check(_lib.flic_server_drain(srv.ptr, float(timeout_s)))
+
+
+def flic_server_stats(srv: Server) -> dict:
+    out = (ctypes.c_int64 * 8)()
+    _check(_lib.flic_server_stats(srv.ptr, out))
+    keys = ["submitted", "rejected", "completed", "batches", "largest_batch", "slots",
+            "slot_bytes", "in_flight"]
+    return dict(zip(keys, [int(x) for x in out]))
+
+
+def flic_server_destroy(srv: Server) -> None:
+    srv.close()
+
+
+def flic_server_clock() -> float:
+    return _lib.flic_server_clock()

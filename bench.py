@@ -17,7 +17,12 @@ Reported (one JSON line on rank 0):
                pixel) / mean launch time vs the measured HBM copy bandwidth
   projection   flic_project + flic_label + flic_scatter on the 128x2048 occlusion frame
                with 262,144 xyz points
+  serving      a short sweep of the continuous-batching server (four Poisson sensors,
+               half of the frames as xyz clouds) at 1,000 / 5,000 / 20,000 frames/s:
+               p50/p99 latency from submission to labels in host memory
   cpu_baseline the CPU oracle (sequential BFS, 1 thread) on all 256 frames once
+The launch shape is autotuned on the batch first (paper_2003_00575_gb300/autotune.py,
+cached as JSON) unless --tuning or --no-autotune is given; config.tuning records it.
 L2 policy: three copies of the batch's buffers (~700 MB, > 129 MB L2) are used in
 rotation, so no step finds its inputs in L2.
 
@@ -64,8 +69,26 @@ def parse_args():
     p.add_argument("--e2e-steps", type=int, default=100)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--tuning", type=str, default="",
-                   help="px_per_cta,threads,cluster,ctas_per_sm for the batch (default: built-in)")
+                   help="px_per_cta,threads,max_strips,ctas_per_sm for the batch (skips autotuning)")
+    p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--serve-seconds", type=float, default=3.0,
+                   help="short serving sweep (0 = skip); the full sweep is serve.py")
     return p.parse_args()
+
+
+def rank_first_seed(rank: int, frames: int) -> int:
+    """Weak scaling: rank r labels the c4 frames with seeds 100 + r*frames ... (disjoint)."""
+    return 100 + rank * frames
+
+
+def reduce_max(dist, value: float, device) -> float:
+    """Max over ranks of a per-rank time (the job is as slow as its slowest rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_env():
@@ -75,12 +98,15 @@ def dist_env():
     return world, rank, local
 
 
+KERNEL_SOURCES = ("flic_label.cu", "flic_device.cuh")
+
+
 def source_sha() -> str:
+    """Hash of the labelling kernel's own sources (what its DRAM traffic depends on)."""
     h = hashlib.sha256()
-    for fn in sorted(os.listdir(CSRC)):
-        if fn.endswith((".cu", ".cuh", ".h")):
-            h.update(fn.encode())
-            h.update(open(os.path.join(CSRC, fn), "rb").read())
+    for fn in KERNEL_SOURCES:
+        h.update(fn.encode())
+        h.update(open(os.path.join(CSRC, fn), "rb").read())
     return h.hexdigest()[:16]
 
 
@@ -228,7 +254,7 @@ def main():
         torch.cuda.synchronize()
 
     # ---- inputs: each rank labels its own 256 frames (weak scaling, no data collective)
-    frames = synth.config_c4(args.frames, first_seed=100 + rank * args.frames)
+    frames = synth.config_c4(args.frames, first_seed=rank_first_seed(rank, args.frames))
     sizes = [f.range.size for f in frames]
     offs = np.concatenate([[0], np.cumsum(sizes)])
     total_px = int(offs[-1])
@@ -250,6 +276,15 @@ def main():
             handles, [rng_dev[k, offs[i]:offs[i + 1]] for i in range(len(frames))],
             [lab_dev[k, offs[i]:offs[i + 1]] for i in range(len(frames))]))
     stream = torch.cuda.current_stream()
+
+    # ---- launch shape: autotuned on these frames (cached as JSON), or given
+    tuned = None
+    if not tun and not args.no_autotune:
+        from paper_2003_00575_gb300 import autotune
+        shapes = [(f.sensor.rows, f.sensor.cols, f.skip) for f in frames]
+        tuned = autotune.tune_batch(flic, batches[0], bargs[0], shapes, stream)
+        for b in batches[1:]:
+            autotune.apply(flic, b, tuned["config"])
 
     # ---- warm-up
     for i in range(max(3, args.warmup)):
@@ -279,11 +314,7 @@ def main():
     t_wall1 = time.perf_counter()
     clocks = sampler.stop()
     step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[args.steps])
-    if dist is not None:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = reduce_max(dist, evs[0].elapsed_time(evs[args.steps]), dev)
     ms_per_step = total_ms / args.steps
     value = total_px * world / (ms_per_step / 1e3) / 1e6
     frames_per_s = len(frames) * world / (ms_per_step / 1e3)
@@ -353,11 +384,7 @@ def main():
         host_out.copy_(lab_dev[0], non_blocking=True)
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1) / e2e_steps
-    if dist is not None:
-        t = torch.tensor([e2e_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
+    e2e_ms = reduce_max(dist, e0.elapsed_time(e1) / e2e_steps, dev)
     e2e = {"value": round(total_px * world / (e2e_ms / 1e3) / 1e6, 1), "unit": UNIT,
            "h2d_bytes_per_step": 4 * total_px, "d2h_bytes_per_step": 4 * total_px,
            "ms_per_step": round(e2e_ms, 4)}
@@ -397,6 +424,22 @@ def main():
     }
     h3.close()
 
+    # ---- short serving sweep: four Poisson sensors, half clouds (the full one: serve.py)
+    serving = None
+    if args.serve_seconds > 0 and world == 1:
+        from paper_2003_00575_gb300 import serve
+        sens = synth.c5_sensors()
+        sh = [flic.flic_create(x.rows, x.cols, x.elevation, x.az_step, 0.5, 3) for x in sens]
+        pool = serve.FramePool(sens, per_kind=2, outputs=128)
+        srv = flic.flic_server_create(sh, pool.max_points, nstreams=2, max_batch=256,
+                                      mem_budget=2 << 30)
+        serve.run_step(flic, srv, pool, 500.0, 0.3, 999)  # first launches capture graphs
+        serving = [serve.run_step(flic, srv, pool, rate, args.serve_seconds / 3, 1000 + i)
+                   for i, rate in enumerate((1000.0, 5000.0, 20000.0))]
+        srv.close()
+        for x in sh:
+            x.close()
+
     # ---- CPU baseline: the oracle as it stands, 1 thread, all frames once (rank 0, N=1)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -426,7 +469,8 @@ def main():
                        "l2": f"inputs larger than L2: {NCOPIES} buffer copies in rotation "
                              f"({NCOPIES * 8 * total_px / 1e6:.0f} MB)",
                        "parallelism": f"frames sharded, {world} rank(s)",
-                       "launch": plan},
+                       "launch": plan,
+                       "tuning": tuned if tuned else (args.tuning or "built-in")},
             "frames_per_s": round(frames_per_s, 1),
             "latency_ms_p50": round(pct(step_ms, 50), 4),
             "latency_ms_p99": round(pct(step_ms, 99), 4),
@@ -435,6 +479,7 @@ def main():
             "e2e": e2e,
             "roofline": roofline,
             "projection": projection,
+            "serving": serving,
             "cpu_baseline": cpu,
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "clock_samples": clocks["samples"],

@@ -41,6 +41,7 @@ struct Tuning {
     int threads = 512;
     int max_strips = flic::kMaxStrips;
     int ctas_per_sm = 0;  // 0 = as many as fit
+    int p3_delay = 2;     // batch: P3 tasks this many waves of blocks after their frame
 };
 
 struct StripPlan {
@@ -590,6 +591,15 @@ flic_status flic_batch_set_tuning(flic_batch b, int32_t px_per_cta, int32_t thre
     return FLIC_OK;
 }
 
+flic_status flic_batch_set_schedule(flic_batch b, int32_t p3_delay_waves) {
+    if (!b || p3_delay_waves < 0 || p3_delay_waves > 64)
+        return fail(FLIC_ERR_INVALID, "p3_delay_waves must be 0..64");
+    if (b->pending) cudaEventSynchronize(b->kernel_done);
+    b->tune.p3_delay = p3_delay_waves;
+    clear_graphs(b);
+    return FLIC_OK;
+}
+
 flic_status flic_batch_last_plan(flic_batch b, int32_t* info) {
     if (!b || !info) return fail(FLIC_ERR_INVALID, "NULL argument");
     std::memcpy(info, b->last_info, sizeof(b->last_info));
@@ -679,7 +689,7 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
                 emit_p3(pending[next_pending++].second);
         }
         const bool border = plans[fi].nstrips > 1 || hs[fi]->wrap;
-        if (border) pending.push_back({p1_count + 2 * resident, fi});
+        if (border) pending.push_back({p1_count + t.p3_delay * resident, fi});
     }
     while (next_pending < pending.size()) emit_p3(pending[next_pending++].second);
     const int ntasks = nt;

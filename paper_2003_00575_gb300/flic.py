@@ -54,6 +54,7 @@ SIGNATURES = {
     "flic_batch_destroy": (_I32, [_P]),
     "flic_set_tuning": (_I32, [_P, _I32, _I32, _I32]),
     "flic_batch_set_tuning": (_I32, [_P, _I32, _I32, _I32, _I32]),
+    "flic_batch_set_schedule": (_I32, [_P, _I32]),
     "flic_plan_info": (_I32, [_P, _P]),
     "flic_plan_frame": (_I32, [_I32, _I32, _I32, _I32, _I32, _P]),
     "flic_batch_last_plan": (_I32, [_P, _P]),
@@ -252,6 +253,10 @@ def flic_batch_destroy(b: Batch) -> None:
 def flic_batch_set_tuning(b: Batch, px_per_cta: int = 0, threads: int = 0, max_strips: int = 0,
                           ctas_per_sm: int = 0) -> None:
     _check(_lib.flic_batch_set_tuning(b.ptr, px_per_cta, threads, max_strips, ctas_per_sm))
+
+
+def flic_batch_set_schedule(b: Batch, p3_delay_waves: int = 2) -> None:
+    _check(_lib.flic_batch_set_schedule(b.ptr, p3_delay_waves))
 
 
 def flic_batch_last_plan(b: Batch) -> dict:

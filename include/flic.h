@@ -272,6 +272,9 @@ flic_status flic_debug_set_iter_limit(flic_handle h, int32_t limit);
  *   Both host buffers must stay valid until the frame's completion is polled; pinned
  *   (page-locked) buffers keep the copies asynchronous.  FLIC_ERR_BUSY when max_queue
  *   requests are already waiting (counted as rejected).
+ * flic_server_hold — hold != 0 pauses admission (requests keep queueing, nothing new
+ *   is launched; batches already in flight finish); 0 resumes.  Lets a caller that knows
+ *   frames arrive together have them labelled in one launch.
  * flic_server_poll — move up to max completion records to out (non-blocking); returns
  *   the number moved.
  * flic_server_drain — wait until every submitted frame has completed (or timeout_s).
@@ -297,6 +300,7 @@ flic_status flic_server_create(const flic_handle* sensors, int32_t nsensors,
                                int64_t mem_budget, int32_t max_queue, flic_server* out);
 flic_status flic_server_submit(flic_server s, int32_t sensor, int32_t kind, const void* host_in,
                                int64_t n, int32_t* host_out, uint64_t tag);
+flic_status flic_server_hold(flic_server s, int32_t hold);
 int32_t flic_server_poll(flic_server s, flic_completion* out, int32_t max);
 flic_status flic_server_drain(flic_server s, double timeout_s);
 flic_status flic_server_stats(flic_server s, int64_t* out);

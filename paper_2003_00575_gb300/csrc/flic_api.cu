@@ -328,7 +328,7 @@ flic_status flic_create_ex(int32_t rows, int32_t cols, const double* elevation, 
     cudaGetDevice(&h->device);
 
     flic_status st;
-    cudaError_t e = flic::label_kernel_setup(std::min((size_t)device_max_smem() - 256, flic::kMaxDynSmem));
+    cudaError_t e = flic::label_kernel_setup(std::min((size_t)device_max_smem() - 1024, flic::kMaxDynSmem));
     if (e != cudaSuccess) { free_ctx(h); return cuda_fail(e, "kernel attributes"); }
 
     build_k_tables(rows, elevation, az_step, skip, h->h_kv, h->h_kh);
@@ -541,7 +541,7 @@ flic_status flic_batch_create(int32_t max_frames, flic_batch* out) {
         flic_batch_destroy(b);
         return cuda_fail(e, "flic_batch_create");
     }
-    if ((e = flic::label_kernel_setup(std::min((size_t)device_max_smem() - 256, flic::kMaxDynSmem))) != cudaSuccess) {
+    if ((e = flic::label_kernel_setup(std::min((size_t)device_max_smem() - 1024, flic::kMaxDynSmem))) != cudaSuccess) {
         flic_batch_destroy(b);
         return cuda_fail(e, "kernel attributes");
     }

@@ -32,6 +32,23 @@ __device__ __forceinline__ bool edge_pred(float a, float b, float K, float delta
     return d2 <= delta2;
 }
 
+// Two edge tests that share the first reading a — (a, b0, K0) and (a, b1, K1) — as one
+// chain of packed fp32x2 operations (sub, mul, mul, mul, add, each element rounded to
+// nearest on its own, exactly the scalar sequence of edge_pred): d2 of each pair.
+__device__ __forceinline__ void edge_d2_pair(float a, float b0, float b1, float K0, float K1,
+                                             float& d0, float& d1) {
+    unsigned long long A, B, KK, t, tt, ab, kab, d2;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(A) : "f"(a));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(B) : "f"(b0), "f"(b1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(KK) : "f"(K0), "f"(K1));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(A), "l"(B));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(tt) : "l"(t));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(ab) : "l"(A), "l"(B));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(kab) : "l"(KK), "l"(ab));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d2) : "l"(tt), "l"(kab));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d0), "=f"(d1) : "l"(d2));
+}
+
 __device__ __forceinline__ void report_timeout(int32_t* status) {
     if (status) atomicExch(status, kStatusTimeout);
 }

@@ -78,7 +78,7 @@ inline size_t strip_smem_bytes(int rows, int pitch_log2, int width, int skip) {
 
 // Dynamic shared memory one block may use (227 KB opt-in on sm_100/sm_103, minus the
 // kernel's static shared memory).
-constexpr size_t kMaxDynSmem = 227 * 1024 - 256;
+constexpr size_t kMaxDynSmem = 227 * 1024 - 1024;
 
 // Kernel launchers (flic_label.cu / flic_project.cu).  Return cudaGetLastError().
 cudaError_t launch_label(const LabelLaunch& L, int grid, int threads, size_t smem,

@@ -331,15 +331,16 @@ __device__ void mask_rows(const Strip& s, const Carve& sm) {
             const bool va = valid_range(a);
             unsigned m = 0;
             if (va) {
+                // with a valid, a neighbour b is a measurement iff b > 0: +inf and NaN
+                // fail d2 <= delta2 by themselves
 #pragma unroll
                 for (int k = 1; k <= S; ++k) {
                     const float b = row[c + k];
-                    if (valid_range(b) && edge_pred(a, b, kh[k - 1], s.delta2)) m |= 1u << (k - 1);
-                    if (k <= down) {
-                        const float d = row[c + k * s.RP];
-                        if (valid_range(d) && edge_pred(a, d, kv[k - 1], s.delta2))
-                            m |= 1u << (8 + k - 1);
-                    }
+                    const float d = k <= down ? row[c + k * s.RP] : 0.0f;
+                    float dh, dv;
+                    edge_d2_pair(a, b, d, kh[k - 1], kv[k - 1], dh, dv);
+                    if (b > 0.0f && dh <= s.delta2) m |= 1u << (k - 1);
+                    if (d > 0.0f && dv <= s.delta2) m |= 1u << (8 + k - 1);
                 }
             }
             const unsigned vm = __ballot_sync(kFull, va);
@@ -448,6 +449,7 @@ __device__ void phase1_local(const Strip& s, const Carve& sm) {
     // c/d. every pixel's label: the global index of its strip-local root
     {
         const volatile int* vp = par;
+        int last_p = -1, last_root = -1;
         const int lane = threadIdx.x & 31;
         const int warp = threadIdx.x >> 5;
         const int nwarps = blockDim.x >> 5;
@@ -463,11 +465,15 @@ __device__ void phase1_local(const Strip& s, const Carve& sm) {
                     int p = c + q < s.W ? vp[base + c + q] : -1;
                     if (p >= 0) {
                         // read-only walk to the strip-local root (paths are short after the
-                        // band pass; nothing writes par any more)
-                        int budget = s.limit;
-                        p = find_smem_ro(vp, p, budget);
-                        if (budget <= 0) report_timeout(s.status);
-                        v[q] = global_of(s, p);
+                        // band pass; nothing writes par any more); neighbours usually share
+                        // their parent, so the last walk is remembered
+                        if (p != last_p) {
+                            int budget = s.limit;
+                            last_root = global_of(s, find_smem_ro(vp, p, budget));
+                            if (budget <= 0) report_timeout(s.status);
+                            last_p = p;
+                        }
+                        v[q] = last_root;
                     } else {
                         v[q] = -1;
                     }
@@ -489,8 +495,13 @@ __device__ void phase1_local(const Strip& s, const Carve& sm) {
 // are rows; each lane loads its row's S readings and labels on both sides of the border
 // at once, tests the crossing edges, and of consecutive rows that would unite the same
 // pair of strip-local roots only the first asks.
+__device__ __forceinline__ unsigned long long volatile_load_u64(const unsigned long long* p) {
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
 template <int S>
-__device__ void border_merge_s(const FrameDesc& f, int b, int limit) {
+__device__ void border_merge_s(const FrameDesc& f, int b, int limit,
+                               unsigned long long* pair_set) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -533,9 +544,16 @@ __device__ void border_merge_s(const FrameDesc& f, int b, int limit) {
                 const bool dup = (lane > 0 && ((em >> (lane - 1)) & 1u) && pa == ga && pb == gb) ||
                                  (ga == done_a && gb == done_b);
                 if (e && !dup && ga != gb) {
-                    int budget = limit;
-                    union_global(f.labels, ga, gb, budget);
-                    if (budget <= 0) report_timeout(f.status);
+                    // the other warps of this block may have united this pair already
+                    const unsigned long long key =
+                        ((unsigned long long)(unsigned)ga << 32) | (unsigned)gb;
+                    const int h = (int)((key * 0x9E3779B97F4A7C15ull) >> 58);  // 64 entries
+                    if (volatile_load_u64(pair_set + h) != key) {
+                        int budget = limit;
+                        union_global(f.labels, ga, gb, budget);
+                        if (budget <= 0) report_timeout(f.status);
+                        pair_set[h] = key;
+                    }
                     done_a = ga;
                     done_b = gb;
                 }
@@ -566,20 +584,25 @@ __device__ void border_merge_narrow(const FrameDesc& f, int limit) {
 
 __device__ void border_merge(const FrameDesc& f, int b) {
     const int limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
+    // root pairs this block has united during this merge (a cache: a collision only
+    // costs a repeated union)
+    __shared__ unsigned long long pair_set[64];
+    for (int i = threadIdx.x; i < 64; i += blockDim.x) pair_set[i] = ~0ull;
+    __syncthreads();
     const int W = min(f.strip_w, f.cols - b * f.strip_w);
     if (W < f.skip) {
         border_merge_narrow(f, limit);
         return;
     }
     switch (f.skip) {
-        case 1: border_merge_s<1>(f, b, limit); break;
-        case 2: border_merge_s<2>(f, b, limit); break;
-        case 3: border_merge_s<3>(f, b, limit); break;
-        case 4: border_merge_s<4>(f, b, limit); break;
-        case 5: border_merge_s<5>(f, b, limit); break;
-        case 6: border_merge_s<6>(f, b, limit); break;
-        case 7: border_merge_s<7>(f, b, limit); break;
-        default: border_merge_s<8>(f, b, limit); break;
+        case 1: border_merge_s<1>(f, b, limit, pair_set); break;
+        case 2: border_merge_s<2>(f, b, limit, pair_set); break;
+        case 3: border_merge_s<3>(f, b, limit, pair_set); break;
+        case 4: border_merge_s<4>(f, b, limit, pair_set); break;
+        case 5: border_merge_s<5>(f, b, limit, pair_set); break;
+        case 6: border_merge_s<6>(f, b, limit, pair_set); break;
+        case 7: border_merge_s<7>(f, b, limit, pair_set); break;
+        default: border_merge_s<8>(f, b, limit, pair_set); break;
     }
 }
 

@@ -97,6 +97,7 @@ struct flic_server_ctx {
     std::vector<flic_completion> completions;
     std::thread dispatcher;
     std::atomic<bool> stop{false};
+    std::atomic<bool> hold{false};  // admission paused by flic_server_hold
     int64_t submitted = 0, rejected = 0, completed = 0, batches = 0, largest = 0;
     int in_flight = 0;
     int device = 0;
@@ -313,7 +314,7 @@ void dispatch_loop(flic_server_ctx* s) {
                 idle = &ln;
                 break;
             }
-        if (idle) {
+        if (idle && !s->hold.load()) {
             take.clear();
             slots.clear();
             {
@@ -343,7 +344,7 @@ void dispatch_loop(flic_server_ctx* s) {
         }
         if (!did) {
             std::unique_lock<std::mutex> lk(s->mu);
-            if (s->stop.load() && s->queue.empty() && s->in_flight == 0) break;
+            if (s->stop.load() && (s->queue.empty() || s->hold.load()) && s->in_flight == 0) break;
             s->cv.wait_for(lk, std::chrono::microseconds(50));
         }
     }
@@ -377,6 +378,13 @@ extern "C" flic_status flic_server_submit(flic_server s, int32_t sensor, int32_t
     }
     s->queue.push_back(q);
     ++s->submitted;
+    s->cv.notify_all();
+    return FLIC_OK;
+}
+
+extern "C" flic_status flic_server_hold(flic_server s, int32_t hold) {
+    if (!s) return srv_fail(FLIC_ERR_INVALID, "flic_server_hold: NULL server");
+    s->hold.store(hold != 0);
     s->cv.notify_all();
     return FLIC_OK;
 }
@@ -415,6 +423,7 @@ extern "C" flic_status flic_server_stats(flic_server s, int64_t* out) {
 
 extern "C" flic_status flic_server_destroy(flic_server s) {
     if (!s) return FLIC_OK;
+    s->hold.store(false);
     flic_status st = flic_server_drain(s, 30.0);
     s->stop.store(true);
     s->cv.notify_all();

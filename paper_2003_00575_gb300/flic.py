@@ -64,6 +64,7 @@ SIGNATURES = {
     "flic_server_create": (_I32, [_P, _I32, _P, _I32, _I32, _I64, _I32, _P]),
     "flic_server_submit": (_I32, [_P, _I32, _I32, _P, _I64, _P, ctypes.c_uint64]),
     "flic_server_poll": (_I32, [_P, _P, _I32]),
+    "flic_server_hold": (_I32, [_P, _I32]),
     "flic_server_drain": (_I32, [_P, _F64]),
     "flic_server_stats": (_I32, [_P, _P]),
     "flic_server_destroy": (_I32, [_P]),
@@ -355,6 +356,10 @@ def flic_server_submit(srv: Server, sensor: int, kind: int, host_in, host_out, t
     if st not in (FLIC_OK, FLIC_ERR_BUSY):
         _check(st)
     return st
+
+
+def flic_server_hold(srv: Server, hold: bool) -> None:
+    _check(_lib.flic_server_hold(srv.ptr, 1 if hold else 0))
 
 
 def flic_server_poll(srv: Server, max_records: int = 4096):

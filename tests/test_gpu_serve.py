@@ -62,7 +62,10 @@ def test_served_mix_equals_alone(flic):
                                   mem_budget=256 << 20)
     try:
         outs = []
+        flic.flic_server_hold(srv, True)  # the first 24 frames arrive together
         for i, (si, f) in enumerate(frames):
+            if i == 24:
+                flic.flic_server_hold(srv, False)  # the rest stream in behind them
             x = torch.from_numpy((f.range if f.xyz is None else f.xyz).reshape(-1)).pin_memory()
             n = f.range.size if f.xyz is None else f.xyz.shape[0]
             y = torch.full((n,), -77, dtype=torch.int32).pin_memory()

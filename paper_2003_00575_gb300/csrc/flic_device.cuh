@@ -53,51 +53,6 @@ __device__ __forceinline__ void report_timeout(int32_t* status) {
     if (status) atomicExch(status, kStatusTimeout);
 }
 
-// ---- union-find in shared memory (tile-local forest, 16-bit local indices) -------------
-// par[x] == x: root; par[x] < x otherwise (hooking always goes to the smaller index, so
-// the root of a set is its minimum element).  Path halving during finds; a store racing
-// with an atomicMin only replaces one ancestor by another, and a union whose atomicMin
-// lost the race retries with the value it found.
-
-__device__ __forceinline__ int find_smem(volatile int* par, int x, int& budget) {
-    while (true) {
-        int p = par[x];
-        if (p == x) return x;
-        int gp = par[p];
-        if (gp == p) return p;
-        par[x] = gp;
-        x = gp;
-        if (--budget <= 0) return x;
-    }
-}
-
-// Read-only find, for the compression pass: once unions are over, each entry is written
-// only by its owner (with its final root), so no stale ancestor can overwrite a root that
-// another thread has just stored (which a halving store issued from an older read could).
-__device__ __forceinline__ int find_smem_ro(const volatile int* par, int x, int& budget) {
-    int p = par[x];
-    while (p != x) {
-        x = p;
-        p = par[x];
-        if (--budget <= 0) break;
-    }
-    return x;
-}
-
-__device__ __forceinline__ void union_smem(int* par, int a, int b, int& budget) {
-    volatile int* vp = par;
-    while (budget > 0) {
-        a = find_smem(vp, a, budget);
-        b = find_smem(vp, b, budget);
-        if (a == b) return;
-        if (a > b) { int t = a; a = b; b = t; }
-        int old = atomicMin(par + b, a);
-        if (old == b) return;
-        b = old;
-        --budget;
-    }
-}
-
 // ---- union-find in global memory (the labels buffer holds the cross-strip forest) ------
 // Loads bypass L1 (.cg): other blocks write these entries.
 

@@ -11,7 +11,7 @@ namespace flic {
 
 constexpr int kMaxSkip = 8;
 constexpr int kMaxStrips = 64;           // column strips per frame
-constexpr int kMaxStripPixels = 32768;   // rows * pitch of one strip (16-bit match keys)
+constexpr int kMaxStripPixels = 32768;   // rows * pitch of one strip
 constexpr int kDefaultIterLimit = 1 << 20;
 
 // One frame as the labelling kernel sees it.  The strip decomposition is part of the
@@ -65,15 +65,14 @@ struct LabelLaunch {
 
 // Shared memory (bytes) one block needs for a strip of `rows` x `width` columns with
 // local pitch 1 << pitch_log2 and skip S: the staged readings (rows x (width + S) rounded
-// up to 4, later reused as the parent array, rows x pitch ints), the 16-bit edge masks
-// (rows x pitch) and two sets of ballot words (rows x pitch / 32 each).
+// up to 4, later reused as the parent array, rows x pitch ints) and 2S + 1 ballot words
+// per 32-column row segment.
 inline size_t strip_smem_bytes(int rows, int pitch_log2, int width, int skip) {
     size_t pitch = size_t(1) << pitch_log2;
     size_t rp = (size_t(width) + size_t(skip) + 3) & ~size_t(3);
     size_t a = size_t(rows) * (rp > pitch ? rp : pitch) * 4;
-    size_t mask = size_t(rows) * pitch * 2;
-    size_t words = size_t(rows) * (pitch / 32) * 4;  // run ballots + validity ballots
-    return a + mask + 2 * words + 64;
+    size_t words = size_t(rows) * (pitch / 32) * (2 * size_t(skip) + 1) * 4;
+    return a + words + 64;
 }
 
 // Dynamic shared memory one block may use (227 KB opt-in on sm_100/sm_103, minus the

@@ -4,35 +4,36 @@
 // column strips; each strip gives two tasks.
 //
 //   P1 (one block, one strip; edge test + tile-local union in shared memory)
-//      0. the strip's range readings, plus S halo columns on the right (wrapping to
-//         column 0 at the seam), are staged into shared memory: one TMA bulk copy
+//      0. the strip's range readings are staged into shared memory: one TMA bulk copy
 //         (cp.async.bulk) per row completing on an mbarrier, or plain loads when the
 //         frame is not 16-byte aligned;
 //      1. every pixel's 2S edge bits (Eq. 2/3; offsets 1..S right and down, the Map
-//         Connections of §III-B-2) are computed from shared memory into a 16-bit mask
-//         per pixel; the staged readings are dead afterwards and their space becomes
-//         the parent array;
-//      a. each warp takes a 32-column row segment; the offset-1 right bits of the
-//         segment are gathered with __ballot_sync and every pixel's parent is set to
-//         the first pixel of its run, so a run of joined pixels becomes one star
-//         without a single atomic;
-//      b. bands of rows are walked top-down with the labels of the rows above in
-//         registers (phase1_bands below): runs hook under the label they touch, and
-//         only where labels meet is a union-find union made (__match_any_sync dedupe,
-//         shared-memory atomicMin hooking to the smaller index);
-//      c. segment seams: edges that cross a 32-column segment border inside the strip;
-//      d. every pixel's label is written as the global index of its strip-local root (a
-//         read-only walk up its short path), the minimum index of its strip-local
-//         component.
+//         Connections of section III-B-2) are computed from shared memory, lanes =
+//         columns, and gathered with __ballot_sync into 32-bit words per 32-column row
+//         segment: one word of measurements, one per right offset, one per down offset.
+//         The staged readings are dead afterwards and their space becomes the parent
+//         array.  Edges that leave the strip are not recorded (P2 tests them again);
+//      a. from here one thread owns one row segment and works on whole words.  A run of
+//         pixels joined by offset-1 right edges is one union-find node, its first pixel
+//         (run starts = measurements without a right edge from the left neighbour);
+//      b. the thread unites its runs with the runs its other edges reach: offsets 1..S
+//         up (the down words of the rows above), offsets 2..S right inside the segment,
+//         and offsets 1..S into the next segment.  Of all edges that join the same two
+//         runs only the first is taken: the pair is constant between consecutive run
+//         starts of either row, so the words are cut at those bits.  Unions hook the
+//         larger root under the smaller with a shared-memory atomicMin and retry when
+//         they lose a race;
+//      c. every pixel's label is written as the global index of its run's strip-local
+//         root (a read-only walk), the minimum index of its strip-local component.
 //         A root's own entry is itself, so the labels buffer now holds a forest of
 //         depth one per strip: the cross-strip forest needs no other memory.
-//      The block that completes the last P1 task of a frame (atomic counter, fenced)
-//      then runs the frame's boundary merge:
-//   P2 (one block per frame; global memory): every edge that leaves a strip on the
-//      right (offsets 1..S, including the azimuth wrap from the last column to the
+//      A strip then arrives at its (up to two) borders; the block that arrives second
+//      at a border merges it:
+//   P2 (one block, one border; global memory): every edge that crosses the border to
+//      the right (offsets 1..S, including the azimuth wrap from the last column to the
 //      first) unites the two strip-local roots with atomicMin hooking and path halving;
-//      rows that ask for the same pair of roots are merged in the warp first.  The
-//      block then raises the frame's ready flag.
+//      rows that ask for the same pair of roots are merged in the warp first.  The block
+//      that merges a frame's last border raises the frame's ready flag.
 //   P3 (one block, one strip; flatten): waits for the frame's ready flag, then every
 //      pixel whose strip-local root was hooked by P2 gets the root of its tree (a
 //      read-only find): label = minimum linear index of the component; -1 stays -1.
@@ -63,7 +64,6 @@ struct Strip {
     int R, C, S;
     float delta2;
     bool wrap;
-    bool border;   // edges can leave the strip (several strips or wrap-around)
     int c0, W;     // first column and width of the strip
     int sh;        // local pitch = 1 << sh (>= 32, >= W)
     int RP;        // row pitch of the staged readings (>= W + S, multiple of 4)
@@ -72,12 +72,13 @@ struct Strip {
 };
 
 // Shared-memory carve-up of one strip (byte offsets; see strip_smem_bytes on the host).
+// Row segment u = r * (P / 32) + seg covers local pixels 32u .. 32u + 31 and owns 2S + 1
+// ballot words: [0] measurements, [k] edge to the pixel k columns right, [S + k] edge to
+// the pixel k rows down (k = 1..S).
 struct Carve {
-    float* stage;       // R x RP staged readings; reused as the parent array (R x P)
+    float* stage;      // R x RP staged readings; reused as the parent array (R x P)
     int* par;
-    uint16_t* mask;     // R x P edge bits
-    unsigned* hmask;    // R x P/32 ballot words of the offset-1 right bits
-    unsigned* vmask;    // R x P/32 ballot words: the pixel is a measurement
+    unsigned* words;   // R x P/32 row segments x (2S + 1) words
 };
 
 __device__ __forceinline__ Carve carve(unsigned char* base, const Strip& s) {
@@ -86,9 +87,7 @@ __device__ __forceinline__ Carve carve(unsigned char* base, const Strip& s) {
     const int a_words = s.R * (s.RP > P ? s.RP : P);
     c.stage = reinterpret_cast<float*>(base);
     c.par = reinterpret_cast<int*>(base);
-    c.mask = reinterpret_cast<uint16_t*>(base + 4 * (size_t)a_words);
-    c.hmask = reinterpret_cast<unsigned*>(base + 4 * (size_t)a_words + 2 * (size_t)s.R * P);
-    c.vmask = c.hmask + (s.R << (s.sh - 5));
+    c.words = reinterpret_cast<unsigned*>(base + 4 * (size_t)a_words);
     return c;
 }
 
@@ -96,223 +95,109 @@ __device__ __forceinline__ int global_of(const Strip& s, int local) {
     return (local >> s.sh) * s.C + s.c0 + (local & ((1 << s.sh) - 1));
 }
 
-// Union of two pixels of the strip (the caller has already dropped redundant requests).
+// ---- word helpers ------------------------------------------------------------------------
+
+// Bits 0..c of a word (c in 0..31).
+__device__ __forceinline__ unsigned upto(int c) { return (2u << c) - 1u; }
+
+// Index of the highest set bit (x != 0).
+__device__ __forceinline__ int top_bit(unsigned x) { return 31 - __clz(x); }
+
+// Run starts of a row segment: measurements that no offset-1 edge reaches from the left.
+__device__ __forceinline__ unsigned run_starts(const unsigned* w) { return w[0] & ~(w[1] << 1); }
+
+// x without its bits below the lowest bit of `cuts` above column c (empty if none).
+__device__ __forceinline__ unsigned skip_to_next(unsigned x, unsigned cuts, int c) {
+    const unsigned nb = cuts & ~upto(c);
+    return x & ~((nb & (0u - nb)) - 1u);
+}
+
+// ---- the strip-local forest ----------------------------------------------------------------
+// Nodes are local pixel indices (r * P + c); only run starts are ever nodes.  par[x] == x:
+// root; par[x] < x otherwise (hooking always goes to the smaller index, so the root of a
+// set is its minimum element).  Node x lives at slot(x): its column bits are XORed with
+// the low bits of its row segment, so that the first pixels of 32 consecutive segments
+// (the commonest run starts) fall into 32 different banks.
+
+__device__ __forceinline__ int slot(int x) { return x ^ ((x >> 5) & 31); }
+
+// Find with path halving.  A halving store racing with an atomicMin only replaces one
+// ancestor by another; a union whose atomicMin lost the race retries with what it found.
+__device__ __forceinline__ int find_run(volatile int* par, int x, int& budget) {
+    while (true) {
+        const int p = par[slot(x)];
+        if (p == x) return x;
+        const int gp = par[slot(p)];
+        if (gp == p) return p;
+        par[slot(x)] = gp;
+        x = gp;
+        if (--budget <= 0) return x;
+    }
+}
+
+// Read-only find, once no union is running any more.
+__device__ __forceinline__ int find_run_ro(const volatile int* par, int x, int& budget) {
+    int p = par[slot(x)];
+    while (p != x) {
+        x = p;
+        p = par[slot(x)];
+        if (--budget <= 0) break;
+    }
+    return x;
+}
+
 __device__ __forceinline__ void unite(int* par, int a, int b, const Strip& s) {
+    volatile int* vp = par;
     int budget = s.limit;
-    union_smem(par, a, b, budget);
+    while (budget > 0) {
+        a = find_run(vp, a, budget);
+        b = find_run(vp, b, budget);
+        if (a == b) break;
+        if (a > b) {
+            const int t = a;
+            a = b;
+            b = t;
+        }
+        const int old = atomicMin(par + slot(b), a);
+        if (old == b) break;
+        b = old;
+        --budget;
+    }
     if (budget <= 0) report_timeout(s.status);
 }
 
-// Hook the run whose first pixel is `root` (a root, or hooked by this row already) under
-// label x < root: one atomicMin; if the pixel was already hooked elsewhere (old), the
-// two sets are united (the union-find retry step).
-__device__ __forceinline__ void hook(int* par, int root, int x, const Strip& s) {
-    const int old = atomicMin(par + root, x);
-    if (old != root && old != x) unite(par, old, x, s);
-}
-
-// b. every edge inside the strip that the runs do not already cover.  Each warp walks a
-//    band of consecutive rows of one 32-column segment from the top down and keeps, in
-//    registers, the labels and edge masks of the S rows above each of its columns.  A
-//    run whose vertical edges all reach pixels of one label X (the common case: ground,
-//    walls) just hooks its first pixel under X with one atomicMin; only where several
-//    labels meet are real unions needed, one per distinct (run, label) pair, found with
-//    __match_any_sync.  Edges that leave the band or the segment use plain unions, with
-//    the requests a neighbouring lane already covers dropped by ballot bit tricks.
-template <int S>
-__device__ void phase1_bands(const Strip& s, const Carve& sm) {
-    constexpr int kInf = 0x7fffffff;
+// 0. Stage the strip's readings into shared memory (row pitch RP).
+__device__ void phase1_stage(const Strip& s, const Carve& sm, uint64_t* bar, uint32_t parity) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    const int segs_log2 = s.sh - 5;
-    const int nseg = 1 << segs_log2;
-    int* par = sm.par;
-    const int band = (s.R * nseg + nwarps - 1) / nwarps;  // rows per band
-    const int nbands = (s.R + band - 1) / band;
-    const unsigned lane_lt = (1u << lane) - 1u;
-
-    for (int blk = warp; blk < nbands * nseg; blk += nwarps) {
-        const int seg = blk & (nseg - 1);
-        const int r0 = (blk >> segs_log2) * band;
-        const int r1 = min(s.R, r0 + band);
-        const int c = (seg << 5) + lane;
-        const bool inw = c < s.W;
-        int lab[S];        // lab[k-1]: a label (set member) of pixel (r-k, c), -1 if none
-        unsigned mab[S];   // mab[k-1]: edge mask of pixel (r-k, c)
-#pragma unroll
-        for (int k = 0; k < S; ++k) {
-            lab[k] = -1;
-            mab[k] = 0u;
+    if (s.bulk) {
+        if (warp == 0) {
+            // the previous item used this memory through ordinary loads and stores
+            fence_proxy_async_smem();
+            if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(s.R * s.W * 4));
+            __syncwarp();
+            for (int r = lane; r < s.R; r += 32)
+                bulk_copy_g2s(sm.stage + r * s.RP, s.range + (size_t)r * s.C + s.c0,
+                              (uint32_t)(s.W * 4), bar);
+            if (!mbar_wait(bar, parity, 1 << 22)) {
+                report_timeout(s.status);
+                mbar_wait(bar, parity, 1 << 22);  // let the copies in flight land
+            }
         }
-        for (int r = r0; r < r1; ++r) {
-            const int u = (r << segs_log2) + seg;
-            const int base = (r << s.sh) + (seg << 5);
-            const int i = base + lane;
-            const unsigned mk = inw ? sm.mask[i] : 0u;
-            const unsigned m = sm.hmask[u];
-            const bool va = inw && ((sm.vmask[u] >> lane) & 1u);
-            // this lane's run: first lane st, last lane en, lanes runbits
-            const unsigned below = ~m & lane_lt;
-            const int st = below ? 32 - __clz(below) : 0;
-            const unsigned brk = (~m | 0x80000000u) & ~lane_lt;
-            const int en = __ffs(brk) - 1;
-            const unsigned runbits = (en == 31 ? kFull : ((2u << en) - 1u)) & ~((1u << st) - 1u);
-            const int sidx = base + st;
-
-            // labels of the pixels above that a vertical edge joins to this pixel: the
-            // smallest in cand, and whether they differ
-            int cand = kInf;
-            bool multi = false;
-#pragma unroll
-            for (int k = 1; k <= S; ++k) {
-                if (r - k < 0) break;
-                if (r - k >= r0) {
-                    if ((mab[k - 1] >> (8 + k - 1)) & 1u) {
-                        const int L = lab[k - 1];
-                        multi |= cand != kInf && L != cand;
-                        cand = min(cand, L);
-                    }
-                } else if (inw) {
-                    // from a row of the band above (another warp): the upper pixel's
-                    // current parent is a member of its set, so it serves as its label
-                    const int ia = ((r - k) << s.sh) + c;
-                    if ((sm.mask[ia] >> (8 + k - 1)) & 1u) {
-                        const int L = ((volatile int*)par)[ia];
-                        multi |= cand != kInf && L != cand;
-                        cand = min(cand, L);
-                    }
-                }
-            }
-            const unsigned hasm = __ballot_sync(kFull, cand != kInf);
-            int mylab = va ? sidx : -1;
-            if (hasm) {
-                const int X = __shfl_sync(kFull, cand, __ffs(hasm) - 1);
-                const unsigned uni = __ballot_sync(kFull, !multi && (cand == kInf || cand == X));
-                if (uni == kFull) {
-                    if (va && (hasm & runbits)) {
-                        mylab = X;
-                        if (lane == st) {
-                            hook(par, sidx, X, s);
-                        } else {
-                            par[i] = X;  // shortcut for the final walk to the root
-                        }
-                    }
-                } else {
-                    // several labels meet.  Lanes are grouped by (run, label); each group's
-                    // first lane hooks the run's first pixel under the label with one
-                    // atomicMin, and only a hook that finds the pixel already hooked
-                    // elsewhere unites the two labels.  A lane with several different
-                    // labels above takes them one offset at a time.
-                    const unsigned anymulti = __ballot_sync(kFull, multi);
-                    if (!anymulti) {
-                        const unsigned key =
-                            cand == kInf ? kFull : ((unsigned)st << 16) | (unsigned)cand;
-                        const unsigned grp = __match_any_sync(kFull, key);
-                        if (cand != kInf && (__ffs(grp) - 1) == lane) hook(par, sidx, cand, s);
-                    } else {
-#pragma unroll
-                        for (int k = 1; k <= S; ++k) {
-                            if (r - k < 0) break;
-                            int ck = kInf;
-                            if (r - k >= r0) {
-                                if ((mab[k - 1] >> (8 + k - 1)) & 1u) ck = lab[k - 1];
-                            } else if (inw) {
-                                const int ia = ((r - k) << s.sh) + c;
-                                if ((sm.mask[ia] >> (8 + k - 1)) & 1u)
-                                    ck = ((volatile int*)par)[ia];
-                            }
-                            const unsigned key =
-                                ck == kInf ? kFull : ((unsigned)st << 16) | (unsigned)ck;
-                            const unsigned grp = __match_any_sync(kFull, key);
-                            if (ck != kInf && (__ffs(grp) - 1) == lane) hook(par, sidx, ck, s);
-                        }
-                    }
-                    __syncwarp();
-                    // the run's label: whatever its first pixel now points to
-                    const int lbl = (va && lane == st) ? ((volatile int*)par)[sidx] : 0;
-                    const int runlab = __shfl_sync(kFull, lbl, st);
-                    if (va) {
-                        mylab = runlab;
-                        if (lane != st) par[i] = runlab;
-                    }
-                }
-            }
-
-            // offsets 2..S along the row, inside the segment (edges into the next
-            // segment are left to the seam pass); nothing to do when both runs already
-            // carry the same label
-#pragma unroll
-            for (int k = 2; k <= S; ++k) {
-                const int stp = __shfl_down_sync(kFull, st, k);      // run start of lane + k
-                const int labp = __shfl_down_sync(kFull, mylab, k);  // its label
-                const bool e_in = ((mk >> (k - 1)) & 1u) && c + k < s.W && lane + k <= 31 &&
-                                  stp != st && labp != mylab;
-                const unsigned eb = __ballot_sync(kFull, e_in);
-                if (e_in) {
-                    // implied by lane l-1 when l-1 ~ l and l-1+k ~ l+k by runs
-                    const bool imp = lane > 0 && ((eb >> (lane - 1)) & 1u) &&
-                                     ((m >> (lane - 1)) & 1u) && ((m >> (lane + k - 1)) & 1u);
-                    if (!imp) unite(par, sidx, base + stp, s);
-                }
-            }
-
-#pragma unroll
-            for (int k = S - 1; k > 0; --k) {
-                lab[k] = lab[k - 1];
-                mab[k] = mab[k - 1];
-            }
-            lab[0] = mylab;
-            mab[0] = mk;
-        }
+    } else {
+        for (int r = warp; r < s.R; r += nwarps)
+            for (int c = lane; c < s.W; c += 32)
+                sm.stage[r * s.RP + c] = __ldg(s.range + (size_t)r * s.C + s.c0 + c);
     }
+    __syncthreads();
 }
 
-// Edges that cross a 32-column segment border inside the strip (offsets 1..S to the
-// right), after the band pass.  Lanes are rows; the pair to unite is the current parents
-// of the two ends, and of consecutive rows asking for the same pair only the first asks.
-__device__ void phase1_seams(const Strip& s, const Carve& sm) {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    volatile int* vp = sm.par;
-    const int nborders = (s.W - 1) >> 5;  // segment borders g | g+1 with (g+1)*32 < W
-    const int rblocks = (s.R + 31) >> 5;
-    for (int job = warp; job < nborders * rblocks; job += nwarps) {
-        const int g = job / rblocks;
-        const int r = ((job - g * rblocks) << 5) + lane;
-        const bool row_ok = r < s.R;
-        const int cb = (g + 1) << 5;  // first column of the next segment
-        int done_a = -1, done_b = -1;  // the last pair this lane united
-        for (int c = cb - s.S; c < cb; ++c) {
-            const unsigned mk = row_ok ? sm.mask[(r << s.sh) + c] : 0u;
-            for (int k = cb - c; k <= s.S; ++k) {
-                const bool e = ((mk >> (k - 1)) & 1u) && c + k < s.W;
-                int a = 0, b = 0;
-                if (e) {
-                    a = vp[(r << s.sh) + c];
-                    b = vp[(r << s.sh) + c + k];
-                }
-                const int pa = __shfl_up_sync(kFull, a, 1);
-                const int pb = __shfl_up_sync(kFull, b, 1);
-                const unsigned em = __ballot_sync(kFull, e);
-                const bool dup = (lane > 0 && ((em >> (lane - 1)) & 1u) && pa == a && pb == b) ||
-                                 (a == done_a && b == done_b);
-                if (e && !dup && a != b) {
-                    unite(sm.par, a, b, s);
-                    done_a = a;
-                    done_b = b;
-                }
-            }
-        }
-    }
-}
-
-// Edge bits of every pixel from the staged readings: bit k-1 = edge to the pixel k
-// columns right (into the halo at the strip's right edge), bit 8+k-1 = edge to the pixel
-// k rows down; validity as one ballot word per 32-column segment.
+// 1. The ballot words of every row segment from the staged readings.  Right edges whose
+//    far end lies past the strip are left out (the boundary merge tests them).
 template <int S>
 __device__ void mask_rows(const Strip& s, const Carve& sm) {
+    constexpr int NP = 2 * S + 1;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -325,168 +210,211 @@ __device__ void mask_rows(const Strip& s, const Carve& sm) {
         }
         const int down = min(S, s.R - 1 - r);  // vertical offsets that stay in the frame
         const float* row = sm.stage + r * s.RP;
+        unsigned* wrow = sm.words + (size_t)(r << (s.sh - 5)) * NP;
         for (int cs = 0; cs < s.W; cs += 32) {  // same trip count on every lane
             const int c = cs + lane;
             const float a = c < s.W ? row[c] : 0.0f;
             const bool va = valid_range(a);
-            unsigned m = 0;
+            bool eh[S], ev[S];
+#pragma unroll
+            for (int k = 0; k < S; ++k) eh[k] = ev[k] = false;
             if (va) {
                 // with a valid, a neighbour b is a measurement iff b > 0: +inf and NaN
-                // fail d2 <= delta2 by themselves
+                // fail d2 <= delta2 by themselves.  row[c + k] stays inside the row pitch
+                // (RP >= W + S); what lies past column W - 1 is never used.
 #pragma unroll
                 for (int k = 1; k <= S; ++k) {
                     const float b = row[c + k];
                     const float d = k <= down ? row[c + k * s.RP] : 0.0f;
                     float dh, dv;
                     edge_d2_pair(a, b, d, kh[k - 1], kv[k - 1], dh, dv);
-                    if (b > 0.0f && dh <= s.delta2) m |= 1u << (k - 1);
-                    if (d > 0.0f && dv <= s.delta2) m |= 1u << (8 + k - 1);
+                    eh[k - 1] = c + k < s.W && b > 0.0f && dh <= s.delta2;
+                    ev[k - 1] = d > 0.0f && dv <= s.delta2;
                 }
             }
-            const unsigned vm = __ballot_sync(kFull, va);
-            if (c < s.W) sm.mask[(r << s.sh) + c] = (uint16_t)m;
-            if (lane == 0) sm.vmask[(r << (s.sh - 5)) + (cs >> 5)] = vm;
-        }
-    }
-}
-
-// Stage the strip and its halo into shared memory and compute the edge masks.
-__device__ void phase1_edges(const Strip& s, const Carve& sm, uint64_t* bar, uint32_t parity) {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-
-    // 0. staging
-    if (s.bulk) {
-        if (warp == 0) {
-            // the previous item used this memory through ordinary loads and stores
-            fence_proxy_async_smem();
-            if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)(s.R * s.W * 4));
-            __syncwarp();
-            for (int r = lane; r < s.R; r += 32)
-                bulk_copy_g2s(sm.stage + r * s.RP, s.range + (size_t)r * s.C + s.c0,
-                              (uint32_t)(s.W * 4), bar);
-        }
-    } else {
-        for (int r = warp; r < s.R; r += nwarps)
-            for (int c = lane; c < s.W; c += 32)
-                sm.stage[r * s.RP + c] = __ldg(s.range + (size_t)r * s.C + s.c0 + c);
-    }
-    // halo: S columns right of the strip (wrapping at the seam; 0 past the last column)
-    for (int t = threadIdx.x; t < s.R * s.S; t += blockDim.x) {
-        const int r = t / s.S;
-        const int j = t - r * s.S;
-        int col = s.c0 + s.W + j;
-        float v = 0.0f;
-        if (col >= s.C && s.wrap) col %= s.C;
-        if (col < s.C) v = __ldg(s.range + (size_t)r * s.C + col);
-        sm.stage[r * s.RP + s.W + j] = v;
-    }
-    if (s.bulk) {
-        if (!mbar_wait(bar, parity, 1 << 22)) {
-            report_timeout(s.status);
-            mbar_wait(bar, parity, 1 << 22);  // let the copies in flight land
-        }
-    }
-    __syncthreads();
-
-    // 1. edge bits of every pixel, from shared memory
-    switch (s.S) {
-        case 1: mask_rows<1>(s, sm); break;
-        case 2: mask_rows<2>(s, sm); break;
-        case 3: mask_rows<3>(s, sm); break;
-        case 4: mask_rows<4>(s, sm); break;
-        case 5: mask_rows<5>(s, sm); break;
-        case 6: mask_rows<6>(s, sm); break;
-        case 7: mask_rows<7>(s, sm); break;
-        default: mask_rows<8>(s, sm); break;
-    }
-    __syncthreads();
-}
-
-__device__ void phase1_local(const Strip& s, const Carve& sm) {
-    const int lane = threadIdx.x & 31;
-    const int warp = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const int segs_log2 = s.sh - 5;
-    const int nunits = s.R << segs_log2;
-    int* par = sm.par;
-    unsigned* hmask = sm.hmask;
-
-    // a. runs of horizontally joined pixels become stars
-    for (int u = warp; u < nunits; u += nwarps) {
-        const int r = u >> segs_log2;
-        const int seg = u & ((1 << segs_log2) - 1);
-        const int c = (seg << 5) + lane;
-        const unsigned mk = c < s.W ? sm.mask[(r << s.sh) + c] : 0u;
-        const bool h1 = (mk & 1u) && c + 1 < s.W;
-        const unsigned m = __ballot_sync(kFull, h1);
-        if (lane == 0) hmask[u] = m;
-        // first lane of this lane's run: one past the highest missing link below it
-        const unsigned below = ~m & ((1u << lane) - 1u);
-        const int start = below ? 32 - __clz(below) : 0;
-        // (validity words of segments that lie wholly past the strip width are never
-        //  written; every lane there has c >= W)
-        const bool va = c < s.W && ((sm.vmask[u] >> lane) & 1u);
-        par[(r << s.sh) + c] = va ? (r << s.sh) + (seg << 5) + start : -1;
-    }
-    __syncthreads();
-
-    switch (s.S) {
-        case 1: phase1_bands<1>(s, sm); break;
-        case 2: phase1_bands<2>(s, sm); break;
-        case 3: phase1_bands<3>(s, sm); break;
-        case 4: phase1_bands<4>(s, sm); break;
-        case 5: phase1_bands<5>(s, sm); break;
-        case 6: phase1_bands<6>(s, sm); break;
-        case 7: phase1_bands<7>(s, sm); break;
-        default: phase1_bands<8>(s, sm); break;
-    }
-    __syncthreads();
-    phase1_seams(s, sm);
-    __syncthreads();
-
-    // c/d. every pixel's label: the global index of its strip-local root
-    {
-        const volatile int* vp = par;
-        int last_p = -1, last_root = -1;
-        const int lane = threadIdx.x & 31;
-        const int warp = threadIdx.x >> 5;
-        const int nwarps = blockDim.x >> 5;
-        const bool vec = ((s.C & 3) == 0) && ((s.c0 & 3) == 0) &&
-                         ((reinterpret_cast<uintptr_t>(s.labels) & 15) == 0);
-        for (int r = warp; r < s.R; r += nwarps) {
-            int32_t* out = s.labels + (size_t)r * s.C + s.c0;
-            const int base = r << s.sh;
-            for (int c = lane * 4; c < s.W; c += 128) {
-                int v[4];
+            // lane p ends up holding word p
+            unsigned mine = __ballot_sync(kFull, va);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    int p = c + q < s.W ? vp[base + c + q] : -1;
-                    if (p >= 0) {
-                        // read-only walk to the strip-local root (paths are short after the
-                        // band pass; nothing writes par any more); neighbours usually share
-                        // their parent, so the last walk is remembered
-                        if (p != last_p) {
-                            int budget = s.limit;
-                            last_root = global_of(s, find_smem_ro(vp, p, budget));
-                            if (budget <= 0) report_timeout(s.status);
-                            last_p = p;
-                        }
-                        v[q] = last_root;
-                    } else {
-                        v[q] = -1;
+            for (int k = 1; k <= S; ++k) {
+                const unsigned wh = __ballot_sync(kFull, eh[k - 1]);
+                const unsigned wv = __ballot_sync(kFull, ev[k - 1]);
+                if (lane == k) mine = wh;
+                if (lane == S + k) mine = wv;
+            }
+            if (lane < NP) wrow[(cs >> 5) * NP + lane] = mine;
+        }
+    }
+}
+
+// a. Every run's first pixel becomes a root of its own (one thread per row segment).
+template <int S>
+__device__ void init_runs(const Strip& s, const Carve& sm) {
+    constexpr int NP = 2 * S + 1;
+    const int nsl = s.sh - 5;
+    const int nunits = s.R << nsl;
+    for (int u = threadIdx.x; u < nunits; u += blockDim.x) {
+        if (((u & ((1 << nsl) - 1)) << 5) >= s.W) continue;  // segment past the strip
+        unsigned x = run_starts(sm.words + (size_t)u * NP);
+        while (x) {
+            const int c = (u << 5) + __ffs(x) - 1;
+            x &= x - 1u;
+            sm.par[slot(c)] = c;
+        }
+    }
+}
+
+// b. Every edge inside the strip that the runs do not already cover, one thread per row
+//    segment.  All edges from the same run to the same run give one union: along a
+//    segment the pair of runs that an offset joins only changes at a run start of either
+//    end, so after an edge at column c the word skips to the next such cut.
+template <int S>
+__device__ void unite_runs(const Strip& s, const Carve& sm) {
+    constexpr int NP = 2 * S + 1;
+    const int nsl = s.sh - 5;
+    const int NS = 1 << nsl;
+    const int nunits = s.R << nsl;
+    int* par = sm.par;
+    for (int u = threadIdx.x; u < nunits; u += blockDim.x) {
+        const int r = u >> nsl;
+        const int seg = u & (NS - 1);
+        if ((seg << 5) >= s.W) continue;
+        const unsigned* wd = sm.words + (size_t)u * NP;
+        const unsigned va = wd[0];
+        if (!va) continue;
+        const unsigned h1 = wd[1];
+        const unsigned rs = va & ~(h1 << 1);
+        const int base = u << 5;
+
+        // offsets 1..S up: the down word k of row r - k joins (r - k, c) and (r, c)
+#pragma unroll
+        for (int k = 1; k <= S; ++k) {
+            if (r - k < 0) break;
+            const unsigned* wu = wd - (size_t)k * NS * NP;
+            unsigned v = wu[S + k];
+            if (!v) continue;
+            const unsigned rsu = run_starts(wu);
+            const unsigned cuts = rs | rsu;
+            const int ubase = base - (k << s.sh);
+            do {
+                const int c = __ffs(v) - 1;
+                const unsigned m = upto(c);
+                unite(par, base + top_bit(rs & m), ubase + top_bit(rsu & m), s);
+                v = skip_to_next(v, cuts, c);
+            } while (v);
+        }
+
+        // offsets 2..S right inside the segment, where the two ends lie in different runs
+        unsigned same = h1;  // bit c: columns c .. c + k joined by offset-1 edges
+#pragma unroll
+        for (int k = 2; k <= S; ++k) {
+            same &= h1 >> (k - 1);
+            unsigned x = wd[k] & ~same & (0xffffffffu >> k);
+            if (!x) continue;
+            const unsigned cuts = rs | (rs >> k);
+            do {
+                const int c = __ffs(x) - 1;
+                unite(par, base + top_bit(rs & upto(c)), base + top_bit(rs & upto(c + k)), s);
+                x = skip_to_next(x, cuts, c);
+            } while (x);
+        }
+
+        // offsets 1..S into the next segment of the row: bit j of word k shifted right by
+        // 32 - k is the edge from column 32 - k + j to column j of the next segment
+        unsigned cross = 0;
+#pragma unroll
+        for (int k = 1; k <= S; ++k) cross |= wd[k] >> (32 - k);
+        if (cross) {
+            const unsigned rsn = run_starts(wd + NP);
+            int la = -1, lb = -1;  // the last pair united
+#pragma unroll
+            for (int k = 1; k <= S; ++k) {
+                unsigned x = wd[k] >> (32 - k);
+                while (x) {
+                    const int j = __ffs(x) - 1;
+                    x &= x - 1u;
+                    const int a = base + top_bit(rs & upto(32 - k + j));
+                    const int b = base + 32 + top_bit(rsn & upto(j));
+                    if (a != la || b != lb) {
+                        unite(par, a, b, s);
+                        la = a;
+                        lb = b;
                     }
                 }
-                if (vec && c + 4 <= s.W) {
-                    __stcg(reinterpret_cast<int4*>(out + c), make_int4(v[0], v[1], v[2], v[3]));
-                } else {
-#pragma unroll
-                    for (int q = 0; q < 4; ++q)
-                        if (c + q < s.W) __stcg(out + c + q, v[q]);
-                }
             }
         }
+    }
+}
+
+// c. Every pixel's label: the global index of its run's strip-local root.  Lanes take four
+//    consecutive pixels of a row (one 16-byte store); neighbours usually share their run,
+//    so the last walk is remembered.
+template <int S>
+__device__ void write_labels(const Strip& s, const Carve& sm) {
+    constexpr int NP = 2 * S + 1;
+    const volatile int* vp = sm.par;
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int nsl = s.sh - 5;
+    const bool vec = ((s.C & 3) == 0) && ((s.c0 & 3) == 0) &&
+                     ((reinterpret_cast<uintptr_t>(s.labels) & 15) == 0);
+    int last_s = -1, last_root = -1;
+    for (int r = warp; r < s.R; r += nwarps) {
+        int32_t* out = s.labels + (size_t)r * s.C + s.c0;
+        for (int c = lane * 4; c < s.W; c += 128) {
+            const int u = (r << nsl) + (c >> 5);
+            const unsigned* wd = sm.words + (size_t)u * NP;
+            const unsigned va = wd[0];
+            const unsigned rs = va & ~(wd[1] << 1);
+            int v[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int cc = (c & 31) + q;  // c is a multiple of 4: same segment
+                v[q] = -1;
+                if ((va >> cc) & 1u) {  // no bit is set at or past column W
+                    const int st = (u << 5) + top_bit(rs & upto(cc));
+                    if (st != last_s) {
+                        int budget = s.limit;
+                        last_root = global_of(s, find_run_ro(vp, st, budget));
+                        if (budget <= 0) report_timeout(s.status);
+                        last_s = st;
+                    }
+                    v[q] = last_root;
+                }
+            }
+            if (vec && c + 4 <= s.W) {
+                __stcg(reinterpret_cast<int4*>(out + c), make_int4(v[0], v[1], v[2], v[3]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (c + q < s.W) __stcg(out + c + q, v[q]);
+            }
+        }
+    }
+}
+
+// Steps 1, a, b and c of a staged strip.
+template <int S>
+__device__ void phase1_strip(const Strip& s, const Carve& sm) {
+    mask_rows<S>(s, sm);
+    __syncthreads();  // the staged readings are dead from here on
+    init_runs<S>(s, sm);
+    __syncthreads();
+    unite_runs<S>(s, sm);
+    __syncthreads();
+    write_labels<S>(s, sm);
+}
+
+__device__ void phase1(const Strip& s, const Carve& sm) {
+    switch (s.S) {
+        case 1: phase1_strip<1>(s, sm); break;
+        case 2: phase1_strip<2>(s, sm); break;
+        case 3: phase1_strip<3>(s, sm); break;
+        case 4: phase1_strip<4>(s, sm); break;
+        case 5: phase1_strip<5>(s, sm); break;
+        case 6: phase1_strip<6>(s, sm); break;
+        case 7: phase1_strip<7>(s, sm); break;
+        default: phase1_strip<8>(s, sm); break;
     }
 }
 
@@ -715,7 +643,6 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
             s.S = f.skip;
             s.delta2 = f.delta2;
             s.wrap = f.wrap != 0;
-            s.border = border;
             s.c0 = si * f.strip_w;
             s.W = min(f.strip_w, s.C - s.c0);
             s.sh = f.pitch_log2;
@@ -724,9 +651,9 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
                      ((reinterpret_cast<uintptr_t>(s.range) & 15) == 0);
             s.limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
             const Carve sm = carve(smem_raw, s);
-            phase1_edges(s, sm, &tma_bar, parity);
+            phase1_stage(s, sm, &tma_bar, parity);
             if (s.bulk) parity ^= 1u;
-            phase1_local(s, sm);
+            phase1(s, sm);
             if (border) {
                 // arrive at the (up to two) borders of this strip; the second arrival at a
                 // border merges it, and the last merged border makes the frame ready

@@ -96,5 +96,5 @@ def test_strip_planner_invariants(lib_path, seed):
     assert P >= max(W, 32) and P & (P - 1) == 0
     assert R * P <= 32768
     rp = (W + S + 3) // 4 * 4
-    assert 4 * R * max(rp, P) + 2 * R * P + 8 * R * (P // 32) + 64 == p["smem"]
+    assert 4 * R * max(rp, P) + 4 * R * (P // 32) * (2 * S + 1) + 64 == p["smem"]
     assert p["smem"] <= 227 * 1024 - 1024

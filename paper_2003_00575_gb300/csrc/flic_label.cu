@@ -15,16 +15,18 @@
 //         array.  Edges that leave the strip are not recorded (P2 tests them again);
 //      a. from here one thread owns one row segment and works on whole words.  A run of
 //         pixels joined by offset-1 right edges is one union-find node, its first pixel
-//         (run starts = measurements without a right edge from the left neighbour);
-//      b. the thread unites its runs with the runs its other edges reach: offsets 1..S
-//         up (the down words of the rows above), offsets 2..S right inside the segment,
-//         and offsets 1..S into the next segment.  Of all edges that join the same two
-//         runs only the first is taken: the pair is constant between consecutive run
-//         starts of either row, so the words are cut at those bits.  Unions hook the
-//         larger root under the smaller with a shared-memory atomicMin and retry when
-//         they lose a race;
-//      c. every pixel's label is written as the global index of its run's strip-local
-//         root (a read-only walk), the minimum index of its strip-local component.
+//         (run starts = measurements without a right edge from the left neighbour).  The
+//         other edges give pairs of runs: of all edges joining the same two runs only the
+//         first is taken (the words are cut at the run starts of both ends), and an edge
+//         of offset k >= 2 that two shorter edges through one pixel already imply is
+//         dropped — on smooth surfaces nearly all of them;
+//      b. every run start is linked to the smallest run its pairs reach (one shared-
+//         memory atomicMin per pair, no finds), which builds most of the forest;
+//      c. every pair is united (finds with path halving, atomicMin hooking of the larger
+//         root under the smaller, retry when a hook loses a race);
+//      d. every run start's entry is set to its root;
+//      e. every pixel's label is written as the global index of its run's strip-local
+//         root, the minimum index of its strip-local component.
 //         A root's own entry is itself, so the labels buffer now holds a forest of
 //         depth one per strip: the cross-strip forest needs no other memory.
 //      A strip then arrives at its (up to two) borders; the block that arrives second
@@ -72,13 +74,10 @@ struct Strip {
 };
 
 // Shared-memory carve-up of one strip (byte offsets; see strip_smem_bytes on the host).
-// Row segment u = r * (P / 32) + seg covers local pixels 32u .. 32u + 31 and owns 2S + 1
-// ballot words: [0] measurements, [k] edge to the pixel k columns right, [S + k] edge to
-// the pixel k rows down (k = 1..S).
 struct Carve {
     float* stage;      // R x RP staged readings; reused as the parent array (R x P)
     int* par;
-    unsigned* words;   // R x P/32 row segments x (2S + 1) words
+    unsigned* words;   // (2S + 1) planes of R x P/32 ballot words
 };
 
 __device__ __forceinline__ Carve carve(unsigned char* base, const Strip& s) {
@@ -97,14 +96,27 @@ __device__ __forceinline__ int global_of(const Strip& s, int local) {
 
 // ---- word helpers ------------------------------------------------------------------------
 
+// The ballot words of a strip, plane-major.  Row segment u = r * P/32 + seg covers local
+// pixels 32u .. 32u + 31; plane p of it is at w[p * n + u] (n = R * P/32): [0] the pixel
+// is a measurement, [k] edge to the pixel k columns right, [S + k] edge to the pixel k
+// rows down (k = 1..S).  Bit j is column 32 seg + j.
+struct Words {
+    unsigned* w;
+    int n;
+    __device__ __forceinline__ unsigned operator()(int p, int u) const { return w[p * n + u]; }
+    // run starts: measurements that no offset-1 edge reaches from the left
+    __device__ __forceinline__ unsigned starts(int u) const { return w[u] & ~(w[n + u] << 1); }
+};
+
+__device__ __forceinline__ Words words_of(const Strip& s, const Carve& sm) {
+    return Words{sm.words, s.R << (s.sh - 5)};
+}
+
 // Bits 0..c of a word (c in 0..31).
 __device__ __forceinline__ unsigned upto(int c) { return (2u << c) - 1u; }
 
 // Index of the highest set bit (x != 0).
 __device__ __forceinline__ int top_bit(unsigned x) { return 31 - __clz(x); }
-
-// Run starts of a row segment: measurements that no offset-1 edge reaches from the left.
-__device__ __forceinline__ unsigned run_starts(const unsigned* w) { return w[0] & ~(w[1] << 1); }
 
 // x without its bits below the lowest bit of `cuts` above column c (empty if none).
 __device__ __forceinline__ unsigned skip_to_next(unsigned x, unsigned cuts, int c) {
@@ -193,14 +205,39 @@ __device__ void phase1_stage(const Strip& s, const Carve& sm, uint64_t* bar, uin
     __syncthreads();
 }
 
-// 1. The ballot words of every row segment from the staged readings.  Right edges whose
-//    far end lies past the strip are left out (the boundary merge tests them).
+// The 2S + 1 ballot words of one 32-column chunk of row `row` (lanes = columns).  An
+// interior chunk has S rows below it and S columns right of it inside the strip, so it
+// needs no bounds tests.  Right edges whose far end lies past the strip are left out (the
+// boundary merge tests them).  With a valid, a neighbour b is a measurement iff b > 0:
+// +inf and NaN fail d2 <= delta2 by themselves.
+template <int S, bool kInterior>
+__device__ __forceinline__ void mask_chunk(const Strip& s, const float* row, int c, int down,
+                                           const float (&kh)[S], const float (&kv)[S],
+                                           unsigned (&w)[2 * S + 1]) {
+    const bool in = kInterior || c < s.W;
+    const float a = in ? row[c] : 0.0f;
+    const bool va = valid_range(a);
+    w[0] = __ballot_sync(kFull, va);
+#pragma unroll
+    for (int k = 1; k <= S; ++k) {
+        const bool hin = kInterior || c + k < s.W;
+        const bool vin = kInterior || (in && k <= down);
+        const float b = hin ? row[c + k] : 0.0f;
+        const float d = vin ? row[c + k * s.RP] : 0.0f;
+        float dh, dv;
+        edge_d2_pair(a, b, d, kh[k - 1], kv[k - 1], dh, dv);
+        w[k] = __ballot_sync(kFull, va & (b > 0.0f) & (dh <= s.delta2));
+        w[S + k] = __ballot_sync(kFull, va & (d > 0.0f) & (dv <= s.delta2));
+    }
+}
+
+// 1. The ballot words of every row segment from the staged readings (a warp per row).
 template <int S>
 __device__ void mask_rows(const Strip& s, const Carve& sm) {
-    constexpr int NP = 2 * S + 1;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
+    const Words wd = words_of(s, sm);
     for (int r = warp; r < s.R; r += nwarps) {
         float kh[S], kv[S];
 #pragma unroll
@@ -210,51 +247,28 @@ __device__ void mask_rows(const Strip& s, const Carve& sm) {
         }
         const int down = min(S, s.R - 1 - r);  // vertical offsets that stay in the frame
         const float* row = sm.stage + r * s.RP;
-        unsigned* wrow = sm.words + (size_t)(r << (s.sh - 5)) * NP;
+        const int u0 = r << (s.sh - 5);
         for (int cs = 0; cs < s.W; cs += 32) {  // same trip count on every lane
-            const int c = cs + lane;
-            const float a = c < s.W ? row[c] : 0.0f;
-            const bool va = valid_range(a);
-            bool eh[S], ev[S];
+            unsigned w[2 * S + 1];
+            if (down == S && cs + 32 + S <= s.W)
+                mask_chunk<S, true>(s, row, cs + lane, down, kh, kv, w);
+            else
+                mask_chunk<S, false>(s, row, cs + lane, down, kh, kv, w);
+            if (lane == 0) {
 #pragma unroll
-            for (int k = 0; k < S; ++k) eh[k] = ev[k] = false;
-            if (va) {
-                // with a valid, a neighbour b is a measurement iff b > 0: +inf and NaN
-                // fail d2 <= delta2 by themselves.  row[c + k] stays inside the row pitch
-                // (RP >= W + S); what lies past column W - 1 is never used.
-#pragma unroll
-                for (int k = 1; k <= S; ++k) {
-                    const float b = row[c + k];
-                    const float d = k <= down ? row[c + k * s.RP] : 0.0f;
-                    float dh, dv;
-                    edge_d2_pair(a, b, d, kh[k - 1], kv[k - 1], dh, dv);
-                    eh[k - 1] = c + k < s.W && b > 0.0f && dh <= s.delta2;
-                    ev[k - 1] = d > 0.0f && dv <= s.delta2;
-                }
+                for (int p = 0; p <= 2 * S; ++p) wd.w[p * wd.n + u0 + (cs >> 5)] = w[p];
             }
-            // lane p ends up holding word p
-            unsigned mine = __ballot_sync(kFull, va);
-#pragma unroll
-            for (int k = 1; k <= S; ++k) {
-                const unsigned wh = __ballot_sync(kFull, eh[k - 1]);
-                const unsigned wv = __ballot_sync(kFull, ev[k - 1]);
-                if (lane == k) mine = wh;
-                if (lane == S + k) mine = wv;
-            }
-            if (lane < NP) wrow[(cs >> 5) * NP + lane] = mine;
         }
     }
 }
 
 // a. Every run's first pixel becomes a root of its own (one thread per row segment).
-template <int S>
 __device__ void init_runs(const Strip& s, const Carve& sm) {
-    constexpr int NP = 2 * S + 1;
+    const Words wd = words_of(s, sm);
     const int nsl = s.sh - 5;
-    const int nunits = s.R << nsl;
-    for (int u = threadIdx.x; u < nunits; u += blockDim.x) {
+    for (int u = threadIdx.x; u < wd.n; u += blockDim.x) {
         if (((u & ((1 << nsl) - 1)) << 5) >= s.W) continue;  // segment past the strip
-        unsigned x = run_starts(sm.words + (size_t)u * NP);
+        unsigned x = wd.starts(u);
         while (x) {
             const int c = (u << 5) + __ffs(x) - 1;
             x &= x - 1u;
@@ -263,94 +277,142 @@ __device__ void init_runs(const Strip& s, const Carve& sm) {
     }
 }
 
-// b. Every edge inside the strip that the runs do not already cover, one thread per row
-//    segment.  All edges from the same run to the same run give one union: along a
-//    segment the pair of runs that an offset joins only changes at a run start of either
-//    end, so after an edge at column c the word skips to the next such cut.
-template <int S>
-__device__ void unite_runs(const Strip& s, const Carve& sm) {
-    constexpr int NP = 2 * S + 1;
+// Every pair of runs (x, y), y < x, that an edge inside the strip joins, for the edges whose
+// near end lies in row segment u: op(x, y).  Of all edges that join the same two runs only
+// the first is taken — along a segment the pair of runs an offset joins only changes at a
+// run start of either end, so after an edge at column c the word skips to the next such
+// cut — and an edge of offset k >= 2 is dropped where two shorter edges through one pixel
+// of the same column (up) or row (right) already join its ends: by induction on k those
+// are taken or dropped for the same reason, so the components do not change.
+template <int S, class Op>
+__device__ __forceinline__ void for_each_pair(const Strip& s, const Words& wd, int u, Op op) {
     const int nsl = s.sh - 5;
     const int NS = 1 << nsl;
-    const int nunits = s.R << nsl;
-    int* par = sm.par;
-    for (int u = threadIdx.x; u < nunits; u += blockDim.x) {
-        const int r = u >> nsl;
-        const int seg = u & (NS - 1);
-        if ((seg << 5) >= s.W) continue;
-        const unsigned* wd = sm.words + (size_t)u * NP;
-        const unsigned va = wd[0];
-        if (!va) continue;
-        const unsigned h1 = wd[1];
-        const unsigned rs = va & ~(h1 << 1);
-        const int base = u << 5;
+    const int r = u >> nsl;
+    const unsigned va = wd(0, u);
+    if (!va) return;
+    const unsigned h1 = wd(1, u);
+    const unsigned rs = va & ~(h1 << 1);
+    const int base = u << 5;
 
-        // offsets 1..S up: the down word k of row r - k joins (r - k, c) and (r, c)
+    // offsets 1..S up: the down word k of row r - k joins (r - k, c) and (r, c)
+#pragma unroll
+    for (int k = 1; k <= S; ++k) {
+        if (r - k < 0) break;
+        const int uu = u - k * NS;
+        unsigned v = wd(S + k, uu);
+        if (k >= 2)  // via (r - 1, c) or via (r - k + 1, c)
+            v &= ~((wd(S + 1, u - NS) & wd(S + k - 1, uu)) |
+                   (wd(S + 1, uu) & wd(S + k - 1, uu + NS)));
+        if (!v) continue;
+        const unsigned rsu = wd.starts(uu);
+        const unsigned cuts = rs | rsu;
+        const int ubase = base - (k << s.sh);
+        do {
+            const int c = __ffs(v) - 1;
+            const unsigned m = upto(c);
+            op(base + top_bit(rs & m), ubase + top_bit(rsu & m));
+            v = skip_to_next(v, cuts, c);
+        } while (v);
+    }
+
+    // offsets 2..S right inside the segment, where the two ends lie in different runs
+    unsigned same = h1;   // bit c: columns c .. c + k joined by offset-1 edges
+    unsigned hprev = h1;  // the right word of offset k - 1
+#pragma unroll
+    for (int k = 2; k <= S; ++k) {
+        same &= h1 >> (k - 1);
+        const unsigned hk = wd(k, u);
+        // via column c + 1 or via column c + k - 1
+        unsigned x = hk & ~same & ~((h1 & (hprev >> 1)) | (hprev & (h1 >> (k - 1)))) &
+                     (0xffffffffu >> k);
+        hprev = hk;
+        if (!x) continue;
+        const unsigned cuts = rs | (rs >> k);
+        do {
+            const int c = __ffs(x) - 1;
+            op(base + top_bit(rs & upto(c + k)), base + top_bit(rs & upto(c)));
+            x = skip_to_next(x, cuts, c);
+        } while (x);
+    }
+
+    // offsets 1..S into the next segment of the row: bit j of right word k shifted right by
+    // 32 - k is the edge from column 32 - k + j to column j of the next segment
+    unsigned cross = 0;
+#pragma unroll
+    for (int k = 1; k <= S; ++k) cross |= wd(k, u) >> (32 - k);
+    if (cross) {
+        const unsigned rsn = wd.starts(u + 1);
+        int la = -1, lb = -1;  // the last pair
 #pragma unroll
         for (int k = 1; k <= S; ++k) {
-            if (r - k < 0) break;
-            const unsigned* wu = wd - (size_t)k * NS * NP;
-            unsigned v = wu[S + k];
-            if (!v) continue;
-            const unsigned rsu = run_starts(wu);
-            const unsigned cuts = rs | rsu;
-            const int ubase = base - (k << s.sh);
-            do {
-                const int c = __ffs(v) - 1;
-                const unsigned m = upto(c);
-                unite(par, base + top_bit(rs & m), ubase + top_bit(rsu & m), s);
-                v = skip_to_next(v, cuts, c);
-            } while (v);
-        }
-
-        // offsets 2..S right inside the segment, where the two ends lie in different runs
-        unsigned same = h1;  // bit c: columns c .. c + k joined by offset-1 edges
-#pragma unroll
-        for (int k = 2; k <= S; ++k) {
-            same &= h1 >> (k - 1);
-            unsigned x = wd[k] & ~same & (0xffffffffu >> k);
-            if (!x) continue;
-            const unsigned cuts = rs | (rs >> k);
-            do {
-                const int c = __ffs(x) - 1;
-                unite(par, base + top_bit(rs & upto(c)), base + top_bit(rs & upto(c + k)), s);
-                x = skip_to_next(x, cuts, c);
-            } while (x);
-        }
-
-        // offsets 1..S into the next segment of the row: bit j of word k shifted right by
-        // 32 - k is the edge from column 32 - k + j to column j of the next segment
-        unsigned cross = 0;
-#pragma unroll
-        for (int k = 1; k <= S; ++k) cross |= wd[k] >> (32 - k);
-        if (cross) {
-            const unsigned rsn = run_starts(wd + NP);
-            int la = -1, lb = -1;  // the last pair united
-#pragma unroll
-            for (int k = 1; k <= S; ++k) {
-                unsigned x = wd[k] >> (32 - k);
-                while (x) {
-                    const int j = __ffs(x) - 1;
-                    x &= x - 1u;
-                    const int a = base + top_bit(rs & upto(32 - k + j));
-                    const int b = base + 32 + top_bit(rsn & upto(j));
-                    if (a != la || b != lb) {
-                        unite(par, a, b, s);
-                        la = a;
-                        lb = b;
-                    }
+            unsigned x = wd(k, u) >> (32 - k);
+            while (x) {
+                const int j = __ffs(x) - 1;
+                x &= x - 1u;
+                const int a = base + top_bit(rs & upto(32 - k + j));
+                const int b = base + 32 + top_bit(rsn & upto(j));
+                if (a != la || b != lb) {
+                    op(b, a);
+                    la = a;
+                    lb = b;
                 }
             }
         }
     }
 }
 
-// c. Every pixel's label: the global index of its run's strip-local root.  Lanes take four
-//    consecutive pixels of a row (one 16-byte store); neighbours usually share their run,
-//    so the last walk is remembered.
+// b. Linking: every run start takes as parent the smallest run that one of its pairs
+//    reaches (shared-memory atomicMin, no finds).  Parents are smaller, so this is a
+//    forest, and most of the strip's structure is in it before any find runs.
 template <int S>
+__device__ void link_runs(const Strip& s, const Carve& sm) {
+    const Words wd = words_of(s, sm);
+    const int nsl = s.sh - 5;
+    int* par = sm.par;
+    for (int u = threadIdx.x; u < wd.n; u += blockDim.x) {
+        if (((u & ((1 << nsl) - 1)) << 5) >= s.W) continue;
+        for_each_pair<S>(s, wd, u, [&](int x, int y) { atomicMin(par + slot(x), y); });
+    }
+}
+
+// c. Every pair united (finds with path halving, atomicMin hooking to the smaller root,
+//    retry when a hook loses a race).
+template <int S>
+__device__ void unite_runs(const Strip& s, const Carve& sm) {
+    const Words wd = words_of(s, sm);
+    const int nsl = s.sh - 5;
+    int* par = sm.par;
+    for (int u = threadIdx.x; u < wd.n; u += blockDim.x) {
+        if (((u & ((1 << nsl) - 1)) << 5) >= s.W) continue;
+        for_each_pair<S>(s, wd, u, [&](int x, int y) { unite(par, x, y, s); });
+    }
+}
+
+// d. Every run start's entry becomes its root (a read-only walk; the only writer of an
+//    entry is the thread of its segment, and it writes the final root).
+__device__ void flatten_runs(const Strip& s, const Carve& sm) {
+    const Words wd = words_of(s, sm);
+    const int nsl = s.sh - 5;
+    volatile int* vp = sm.par;
+    for (int u = threadIdx.x; u < wd.n; u += blockDim.x) {
+        if (((u & ((1 << nsl) - 1)) << 5) >= s.W) continue;
+        unsigned x = wd.starts(u);
+        while (x) {
+            const int node = (u << 5) + __ffs(x) - 1;
+            x &= x - 1u;
+            int budget = s.limit;
+            const int root = find_run_ro(vp, node, budget);
+            if (budget <= 0) report_timeout(s.status);
+            vp[slot(node)] = root;
+        }
+    }
+}
+
+// e. Every pixel's label: the global index of its run's root.  Lanes take four consecutive
+//    pixels of a row (one 16-byte store).
 __device__ void write_labels(const Strip& s, const Carve& sm) {
-    constexpr int NP = 2 * S + 1;
+    const Words wd = words_of(s, sm);
     const volatile int* vp = sm.par;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -363,9 +425,8 @@ __device__ void write_labels(const Strip& s, const Carve& sm) {
         int32_t* out = s.labels + (size_t)r * s.C + s.c0;
         for (int c = lane * 4; c < s.W; c += 128) {
             const int u = (r << nsl) + (c >> 5);
-            const unsigned* wd = sm.words + (size_t)u * NP;
-            const unsigned va = wd[0];
-            const unsigned rs = va & ~(wd[1] << 1);
+            const unsigned va = wd(0, u);
+            const unsigned rs = wd.starts(u);
             int v[4];
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -374,9 +435,7 @@ __device__ void write_labels(const Strip& s, const Carve& sm) {
                 if ((va >> cc) & 1u) {  // no bit is set at or past column W
                     const int st = (u << 5) + top_bit(rs & upto(cc));
                     if (st != last_s) {
-                        int budget = s.limit;
-                        last_root = global_of(s, find_run_ro(vp, st, budget));
-                        if (budget <= 0) report_timeout(s.status);
+                        last_root = global_of(s, vp[slot(st)]);
                         last_s = st;
                     }
                     v[q] = last_root;
@@ -393,16 +452,20 @@ __device__ void write_labels(const Strip& s, const Carve& sm) {
     }
 }
 
-// Steps 1, a, b and c of a staged strip.
+// Steps 1 and a to e of a staged strip.
 template <int S>
 __device__ void phase1_strip(const Strip& s, const Carve& sm) {
     mask_rows<S>(s, sm);
     __syncthreads();  // the staged readings are dead from here on
-    init_runs<S>(s, sm);
+    init_runs(s, sm);
+    __syncthreads();
+    link_runs<S>(s, sm);
     __syncthreads();
     unite_runs<S>(s, sm);
     __syncthreads();
-    write_labels<S>(s, sm);
+    flatten_runs(s, sm);
+    __syncthreads();
+    write_labels(s, sm);
 }
 
 __device__ void phase1(const Strip& s, const Carve& sm) {
@@ -419,10 +482,11 @@ __device__ void phase1(const Strip& s, const Carve& sm) {
 }
 
 // P2: the boundary merge of one border (strip b's right edge, to strip b + 1 or across
-// the seam to strip 0), by the block that completes the second of its two strips.  Lanes
-// are rows; each lane loads its row's S readings and labels on both sides of the border
-// at once, tests the crossing edges, and of consecutive rows that would unite the same
-// pair of strip-local roots only the first asks.
+// the seam to strip 0), by the block that completes the second of its two strips.  The
+// crossing edges are split into items (32 rows, source column first + j, offset k) so
+// that most warps of the block take one: each lane loads its row's two readings and
+// strip-local roots, tests the edge, and of consecutive rows that would unite the same
+// pair of roots only the first asks.
 __device__ __forceinline__ unsigned long long volatile_load_u64(const unsigned long long* p) {
     return *reinterpret_cast<const volatile unsigned long long*>(p);
 }
@@ -430,61 +494,50 @@ __device__ __forceinline__ unsigned long long volatile_load_u64(const unsigned l
 template <int S>
 __device__ void border_merge_s(const FrameDesc& f, int b, int limit,
                                unsigned long long* pair_set) {
+    constexpr int kItems = S * (S + 1) / 2;  // (j, k) with j + k >= S
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const int R = f.rows, C = f.cols;
     const int c0 = b * f.strip_w;
     const int W = min(f.strip_w, C - c0);  // >= S (several strips, or C >= S)
-    const int first = W - S;
+    const int first = c0 + W - S;          // first column that has a crossing edge
     const int rblocks = (R + 31) >> 5;
-    for (int rb = warp; rb < rblocks; rb += nwarps) {
-        const int r = (rb << 5) + lane;
-        const bool row_ok = r < R;
-        const float* rrow = f.range + (size_t)(row_ok ? r : 0) * C;
-        const int32_t* lrow = f.labels + (size_t)(row_ok ? r : 0) * C;
-        float av[S], dv[S], kh[S];
-        int la[S], lb[S];
-        int done_a = -1, done_b = -1;  // the last pair this lane united
-#pragma unroll
-        for (int j = 0; j < S; ++j) {
-            int tc = c0 + W + j;  // j-th column past the border
-            if (tc >= C && f.wrap) tc %= C;
-            const bool tok = row_ok && tc < C;
-            av[j] = row_ok ? load_range(rrow + c0 + first + j) : 0.0f;
-            la[j] = row_ok ? __ldcg(lrow + c0 + first + j) : 0;
-            dv[j] = tok ? load_range(rrow + tc) : 0.0f;
-            lb[j] = tok ? __ldcg(lrow + tc) : 0;
-            kh[j] = __ldg(f.kh + (row_ok ? r : 0) * S + j);
+    for (int item = warp; item < rblocks * kItems; item += nwarps) {
+        const int rb = item / kItems;
+        int q = item - rb * kItems;
+        int j = 0;  // source column first + j has the j + 1 offsets S - j .. S
+        while (q > j) {
+            q -= j + 1;
+            ++j;
         }
-#pragma unroll
-        for (int j = 0; j < S; ++j) {            // source column first + j
-#pragma unroll
-            for (int k = S - j; k <= S; ++k) {   // offsets that cross: target j + k - S
-                const int t = j + k - S;
-                const bool e = av[j] > 0.0f && dv[t] > 0.0f && edge_pred(av[j], dv[t], kh[k - 1], f.delta2);
-                const int ga = la[j], gb = lb[t];
-                const int pa = __shfl_up_sync(kFull, ga, 1);
-                const int pb = __shfl_up_sync(kFull, gb, 1);
-                const unsigned em = __ballot_sync(kFull, e);
-                // dropped when the row above asks for the same pair, or when this row
-                // already asked for it at another column or offset
-                const bool dup = (lane > 0 && ((em >> (lane - 1)) & 1u) && pa == ga && pb == gb) ||
-                                 (ga == done_a && gb == done_b);
-                if (e && !dup && ga != gb) {
-                    // the other warps of this block may have united this pair already
-                    const unsigned long long key =
-                        ((unsigned long long)(unsigned)ga << 32) | (unsigned)gb;
-                    const int h = (int)((key * 0x9E3779B97F4A7C15ull) >> 58);  // 64 entries
-                    if (volatile_load_u64(pair_set + h) != key) {
-                        int budget = limit;
-                        union_global(f.labels, ga, gb, budget);
-                        if (budget <= 0) report_timeout(f.status);
-                        pair_set[h] = key;
-                    }
-                    done_a = ga;
-                    done_b = gb;
-                }
+        const int k = S - j + q;
+        int tc = first + j + k;  // target column, past the border (< C + S <= 2C)
+        if (tc >= C && f.wrap) tc -= C;
+        const int r = (rb << 5) + lane;
+        const bool ok = r < R && tc < C;
+        const int row = (ok ? r : 0) * C;  // frames hold at most 2^21 pixels
+        const float av = ok ? load_range(f.range + row + first + j) : 0.0f;
+        const float dv = ok ? load_range(f.range + row + tc) : 0.0f;
+        const int ga = ok ? __ldcg(f.labels + row + first + j) : 0;
+        const int gb = ok ? __ldcg(f.labels + row + tc) : 0;
+        const float K = __ldg(f.kh + (ok ? r : 0) * S + k - 1);
+        const bool e = av > 0.0f && dv > 0.0f && edge_pred(av, dv, K, f.delta2);
+        const int pa = __shfl_up_sync(kFull, ga, 1);
+        const int pb = __shfl_up_sync(kFull, gb, 1);
+        const unsigned em = __ballot_sync(kFull, e);
+        // dropped when the row above asks for the same pair
+        const bool dup = lane > 0 && ((em >> (lane - 1)) & 1u) && pa == ga && pb == gb;
+        if (e && !dup && ga != gb) {
+            // other lanes and warps of this block may have united this pair already
+            const unsigned long long key =
+                ((unsigned long long)(unsigned)ga << 32) | (unsigned)gb;
+            const int h = (int)((key * 0x9E3779B97F4A7C15ull) >> 58);  // 64 entries
+            if (volatile_load_u64(pair_set + h) != key) {
+                int budget = limit;
+                union_global(f.labels, ga, gb, budget);
+                if (budget <= 0) report_timeout(f.status);
+                pair_set[h] = key;
             }
         }
     }
@@ -534,9 +587,12 @@ __device__ void border_merge(const FrameDesc& f, int b) {
     }
 }
 
-// P3: flatten one strip once its frame's forest is final.  Consecutive pixels usually
-// share a strip-local root, so each thread remembers its last lookup.
+// P3: flatten one strip once its frame's forest is final.  A warp takes pairs of
+// 128-column row chunks and issues their loads before any find, so that the latency of
+// one load round trip covers two chunks; consecutive pixels usually share a
+// strip-local root, so each thread remembers its last lookup.
 __device__ void phase3_strip(const FrameDesc& f, int si) {
+    constexpr int G = 2;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -545,23 +601,36 @@ __device__ void phase3_strip(const FrameDesc& f, int si) {
     const int limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
     const bool vec = ((f.cols & 3) == 0) && ((c0 & 3) == 0) &&
                      ((reinterpret_cast<uintptr_t>(f.labels) & 15) == 0);
+    const int nchunk = (W + 127) >> 7;
+    const int items = f.rows * nchunk;
     int last_l = -1, last_root = -1;
-    for (int r = warp; r < f.rows; r += nwarps) {
-        int32_t* row = f.labels + (size_t)r * f.cols + c0;
-        for (int c = lane * 4; c < W; c += 128) {
-            int v[4];
-            const bool full = vec && c + 4 <= W;
-            if (full) {
+    for (int i0 = warp * G; i0 < items; i0 += nwarps * G) {
+        int v[G][4];
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int it = i0 + g;
+            const int r = it / nchunk;
+            const int c = ((it - r * nchunk) << 7) + lane * 4;
+            const int32_t* row = f.labels + (size_t)r * f.cols + c0;
+            if (it < items && vec && c + 4 <= W) {
                 const int4 x = __ldcg(reinterpret_cast<const int4*>(row + c));
-                v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+                v[g][0] = x.x; v[g][1] = x.y; v[g][2] = x.z; v[g][3] = x.w;
             } else {
 #pragma unroll
-                for (int q = 0; q < 4; ++q) v[q] = c + q < W ? __ldcg(row + c + q) : -1;
+                for (int q = 0; q < 4; ++q)
+                    v[g][q] = it < items && c + q < W ? __ldcg(row + c + q) : -1;
             }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int it = i0 + g;
+            if (it >= items) break;
+            const int r = it / nchunk;
+            const int c = ((it - r * nchunk) << 7) + lane * 4;
             bool changed = false;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const int l = v[q];
+                const int l = v[g][q];
                 if (l < 0) continue;
                 if (l != last_l) {
                     int budget = limit;
@@ -570,17 +639,19 @@ __device__ void phase3_strip(const FrameDesc& f, int si) {
                     last_l = l;
                 }
                 if (last_root != l) {
-                    v[q] = last_root;
+                    v[g][q] = last_root;
                     changed = true;
                 }
             }
             if (changed) {
-                if (full) {
-                    __stcg(reinterpret_cast<int4*>(row + c), make_int4(v[0], v[1], v[2], v[3]));
+                int32_t* row = f.labels + (size_t)r * f.cols + c0;
+                if (vec && c + 4 <= W) {
+                    __stcg(reinterpret_cast<int4*>(row + c),
+                           make_int4(v[g][0], v[g][1], v[g][2], v[g][3]));
                 } else {
 #pragma unroll
                     for (int q = 0; q < 4; ++q)
-                        if (c + q < W) __stcg(row + c + q, v[q]);
+                        if (c + q < W) __stcg(row + c + q, v[g][q]);
                 }
             }
         }

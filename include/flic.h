@@ -209,7 +209,7 @@ flic_status flic_set_tuning(flic_handle h, int32_t px_per_cta, int32_t threads, 
 flic_status flic_batch_set_tuning(flic_batch b, int32_t px_per_cta, int32_t threads,
                                   int32_t max_strips, int32_t ctas_per_sm);
 /* Merge schedule of a batch object: a frame's flatten tasks are queued this many waves of
- * resident blocks after its last strip task (0..64; default 2).  Results never depend
+ * resident blocks after its last strip task (0..64; default 8).  Results never depend
  * on it.  Errors: FLIC_ERR_INVALID. */
 flic_status flic_batch_set_schedule(flic_batch b, int32_t p3_delay_waves);
 

@@ -20,9 +20,9 @@ SPACE = {
     "px_per_cta": [8192, 16384, 32768],
     "threads": [256, 512],
     "ctas_per_sm": [0, 1],
-    "p3_delay": [1, 2, 4],
+    "p3_delay": [2, 4, 8, 16],
 }
-DEFAULT = {"px_per_cta": 16384, "threads": 512, "ctas_per_sm": 0, "p3_delay": 2}
+DEFAULT = {"px_per_cta": 16384, "threads": 512, "ctas_per_sm": 0, "p3_delay": 8}
 
 
 def configs(space: dict = SPACE):

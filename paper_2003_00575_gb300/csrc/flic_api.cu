@@ -41,7 +41,7 @@ struct Tuning {
     int threads = 512;
     int max_strips = flic::kMaxStrips;
     int ctas_per_sm = 0;  // 0 = as many as fit
-    int p3_delay = 2;     // batch: P3 tasks this many waves of blocks after their frame
+    int p3_delay = 8;     // batch: P3 tasks this many waves of blocks after their frame
 };
 
 struct StripPlan {

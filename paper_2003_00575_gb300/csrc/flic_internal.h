@@ -43,7 +43,7 @@ struct Task {
 
 // Queue counters (int32, zero between launches; the kernel's last block re-zeroes them):
 // [kCtrNext] next task, [kCtrExit] blocks done, then kCtrPerFrame per frame f at
-// kCtrFrames + kCtrPerFrame*f: [0] borders merged, [1] frame ready for P3,
+// kCtrFrames + kCtrPerFrame*f: [0] borders merged (P3 waits for all), [1] unused,
 // [2 + b] strips of border b that finished P1.
 constexpr int kCtrNext = 0;
 constexpr int kCtrExit = 1;

@@ -34,17 +34,18 @@
 //   P2 (one block, one border; global memory): every edge that crosses the border to
 //      the right (offsets 1..S, including the azimuth wrap from the last column to the
 //      first) unites the two strip-local roots with atomicMin hooking and path halving;
-//      rows that ask for the same pair of roots are merged in the warp first.  The block
-//      that merges a frame's last border raises the frame's ready flag.
-//   P3 (one block, one strip; flatten): waits for the frame's ready flag, then every
+//      rows that ask for the same pair of roots are merged in the warp first.  Each
+//      merged border is counted (a release reduction); the frame is ready when the
+//      count reaches its number of borders.
+//   P3 (one block, one strip; flatten): waits until its frame is ready, then every
 //      pixel whose strip-local root was hooked by P2 gets the root of its tree (a
 //      read-only find): label = minimum linear index of the component; -1 stays -1.
 //
-// P3 tasks of a frame are queued about one wave of blocks after its P1 tasks, so they
-// seldom wait.  A block only ever waits for tasks that running blocks have already
-// taken and that never wait themselves, so the queue cannot deadlock; the wait is
-// bounded all the same and reports exhaustion in the frame's status word, as does every
-// union and find loop.  The last block to leave resets the queue's counters for the next
+// P3 tasks of a frame are queued a few waves of blocks after its P1 tasks, so they
+// seldom wait.  A block only ever waits for tasks that come before its own in the queue,
+// which running blocks have already taken and which never wait themselves, so the queue
+// cannot deadlock; the wait is bounded all the same and reports exhaustion in the
+// frame's status word, as does every union and find loop.  The last block to leave resets the queue's counters for the next
 // launch.  The labels buffer is the only global working memory besides those counters.
 #include <cstdint>
 
@@ -77,7 +78,7 @@ struct Strip {
 struct Carve {
     float* stage;      // R x RP staged readings; reused as the parent array (R x P)
     int* par;
-    unsigned* words;   // (2S + 1) planes of R x P/32 ballot words
+    unsigned* words;   // R x P/32 row segments x (2S + 1) ballot words
 };
 
 __device__ __forceinline__ Carve carve(unsigned char* base, const Strip& s) {
@@ -96,20 +97,26 @@ __device__ __forceinline__ int global_of(const Strip& s, int local) {
 
 // ---- word helpers ------------------------------------------------------------------------
 
-// The ballot words of a strip, plane-major.  Row segment u = r * P/32 + seg covers local
-// pixels 32u .. 32u + 31; plane p of it is at w[p * n + u] (n = R * P/32): [0] the pixel
+// The ballot words of a strip.  Row segment u = r * P/32 + seg covers local pixels
+// 32u .. 32u + 31 and owns the 2S + 1 consecutive words w[u * (2S + 1) + p]: [0] the pixel
 // is a measurement, [k] edge to the pixel k columns right, [S + k] edge to the pixel k
-// rows down (k = 1..S).  Bit j is column 32 seg + j.
+// rows down (k = 1..S).  Bit j is column 32 seg + j.  The stride 2S + 1 is odd, so 32
+// threads reading the same word of 32 consecutive segments hit 32 different banks.
+template <int S>
 struct Words {
+    static constexpr int NP = 2 * S + 1;
     unsigned* w;
-    int n;
-    __device__ __forceinline__ unsigned operator()(int p, int u) const { return w[p * n + u]; }
+    int n;  // row segments
+    __device__ __forceinline__ unsigned operator()(int p, int u) const { return w[u * NP + p]; }
     // run starts: measurements that no offset-1 edge reaches from the left
-    __device__ __forceinline__ unsigned starts(int u) const { return w[u] & ~(w[n + u] << 1); }
+    __device__ __forceinline__ unsigned starts(int u) const {
+        return w[u * NP] & ~(w[u * NP + 1] << 1);
+    }
 };
 
-__device__ __forceinline__ Words words_of(const Strip& s, const Carve& sm) {
-    return Words{sm.words, s.R << (s.sh - 5)};
+template <int S>
+__device__ __forceinline__ Words<S> words_of(const Strip& s, const Carve& sm) {
+    return Words<S>{sm.words, s.R << (s.sh - 5)};
 }
 
 // Bits 0..c of a word (c in 0..31).
@@ -237,7 +244,7 @@ __device__ void mask_rows(const Strip& s, const Carve& sm) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
-    const Words wd = words_of(s, sm);
+    const Words<S> wd = words_of<S>(s, sm);
     for (int r = warp; r < s.R; r += nwarps) {
         float kh[S], kv[S];
 #pragma unroll
@@ -247,24 +254,30 @@ __device__ void mask_rows(const Strip& s, const Carve& sm) {
         }
         const int down = min(S, s.R - 1 - r);  // vertical offsets that stay in the frame
         const float* row = sm.stage + r * s.RP;
-        const int u0 = r << (s.sh - 5);
-        for (int cs = 0; cs < s.W; cs += 32) {  // same trip count on every lane
+        unsigned* out = wd.w + (size_t)(r << (s.sh - 5)) * Words<S>::NP;
+        // chunks with cs + 32 + S <= W and S rows below are interior
+        const int interior = down == S && s.W >= S ? ((s.W - S) >> 5) << 5 : 0;
+        int cs = 0;
+        for (; cs < interior; cs += 32) {  // same trip counts on every lane
             unsigned w[2 * S + 1];
-            if (down == S && cs + 32 + S <= s.W)
-                mask_chunk<S, true>(s, row, cs + lane, down, kh, kv, w);
-            else
-                mask_chunk<S, false>(s, row, cs + lane, down, kh, kv, w);
-            if (lane == 0) {
+            mask_chunk<S, true>(s, row, cs + lane, down, kh, kv, w);
+            // every lane stores the same word to the same address: one write
 #pragma unroll
-                for (int p = 0; p <= 2 * S; ++p) wd.w[p * wd.n + u0 + (cs >> 5)] = w[p];
-            }
+            for (int p = 0; p <= 2 * S; ++p) out[(cs >> 5) * Words<S>::NP + p] = w[p];
+        }
+        for (; cs < s.W; cs += 32) {
+            unsigned w[2 * S + 1];
+            mask_chunk<S, false>(s, row, cs + lane, down, kh, kv, w);
+#pragma unroll
+            for (int p = 0; p <= 2 * S; ++p) out[(cs >> 5) * Words<S>::NP + p] = w[p];
         }
     }
 }
 
 // a. Every run's first pixel becomes a root of its own (one thread per row segment).
+template <int S>
 __device__ void init_runs(const Strip& s, const Carve& sm) {
-    const Words wd = words_of(s, sm);
+    const Words<S> wd = words_of<S>(s, sm);
     const int nsl = s.sh - 5;
     for (int u = threadIdx.x; u < wd.n; u += blockDim.x) {
         if (((u & ((1 << nsl) - 1)) << 5) >= s.W) continue;  // segment past the strip
@@ -285,7 +298,7 @@ __device__ void init_runs(const Strip& s, const Carve& sm) {
 // of the same column (up) or row (right) already join its ends: by induction on k those
 // are taken or dropped for the same reason, so the components do not change.
 template <int S, class Op>
-__device__ __forceinline__ void for_each_pair(const Strip& s, const Words& wd, int u, Op op) {
+__device__ __forceinline__ void for_each_pair(const Strip& s, const Words<S>& wd, int u, Op op) {
     const int nsl = s.sh - 5;
     const int NS = 1 << nsl;
     const int r = u >> nsl;
@@ -367,7 +380,7 @@ __device__ __forceinline__ void for_each_pair(const Strip& s, const Words& wd, i
 //    forest, and most of the strip's structure is in it before any find runs.
 template <int S>
 __device__ void link_runs(const Strip& s, const Carve& sm) {
-    const Words wd = words_of(s, sm);
+    const Words<S> wd = words_of<S>(s, sm);
     const int nsl = s.sh - 5;
     int* par = sm.par;
     for (int u = threadIdx.x; u < wd.n; u += blockDim.x) {
@@ -380,7 +393,7 @@ __device__ void link_runs(const Strip& s, const Carve& sm) {
 //    retry when a hook loses a race).
 template <int S>
 __device__ void unite_runs(const Strip& s, const Carve& sm) {
-    const Words wd = words_of(s, sm);
+    const Words<S> wd = words_of<S>(s, sm);
     const int nsl = s.sh - 5;
     int* par = sm.par;
     for (int u = threadIdx.x; u < wd.n; u += blockDim.x) {
@@ -391,8 +404,9 @@ __device__ void unite_runs(const Strip& s, const Carve& sm) {
 
 // d. Every run start's entry becomes its root (a read-only walk; the only writer of an
 //    entry is the thread of its segment, and it writes the final root).
+template <int S>
 __device__ void flatten_runs(const Strip& s, const Carve& sm) {
-    const Words wd = words_of(s, sm);
+    const Words<S> wd = words_of<S>(s, sm);
     const int nsl = s.sh - 5;
     volatile int* vp = sm.par;
     for (int u = threadIdx.x; u < wd.n; u += blockDim.x) {
@@ -411,8 +425,9 @@ __device__ void flatten_runs(const Strip& s, const Carve& sm) {
 
 // e. Every pixel's label: the global index of its run's root.  Lanes take four consecutive
 //    pixels of a row (one 16-byte store).
+template <int S>
 __device__ void write_labels(const Strip& s, const Carve& sm) {
-    const Words wd = words_of(s, sm);
+    const Words<S> wd = words_of<S>(s, sm);
     const volatile int* vp = sm.par;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -457,15 +472,15 @@ template <int S>
 __device__ void phase1_strip(const Strip& s, const Carve& sm) {
     mask_rows<S>(s, sm);
     __syncthreads();  // the staged readings are dead from here on
-    init_runs(s, sm);
+    init_runs<S>(s, sm);
     __syncthreads();
     link_runs<S>(s, sm);
     __syncthreads();
     unite_runs<S>(s, sm);
     __syncthreads();
-    flatten_runs(s, sm);
+    flatten_runs<S>(s, sm);
     __syncthreads();
-    write_labels(s, sm);
+    write_labels<S>(s, sm);
 }
 
 __device__ void phase1(const Strip& s, const Carve& sm) {
@@ -587,12 +602,12 @@ __device__ void border_merge(const FrameDesc& f, int b) {
     }
 }
 
-// P3: flatten one strip once its frame's forest is final.  A warp takes pairs of
+// P3: flatten one strip once its frame's forest is final.  A warp takes groups of four
 // 128-column row chunks and issues their loads before any find, so that the latency of
-// one load round trip covers two chunks; consecutive pixels usually share a
+// one load round trip covers four chunks; consecutive pixels usually share a
 // strip-local root, so each thread remembers its last lookup.
 __device__ void phase3_strip(const FrameDesc& f, int si) {
-    constexpr int G = 2;
+    constexpr int G = 4;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
@@ -664,8 +679,8 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
     return v;
 }
 
-__device__ __forceinline__ void st_release(int* p, int v) {
-    asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+__device__ __forceinline__ void red_release_add(int* p, int v) {
+    asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L) {
@@ -673,6 +688,7 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
     __shared__ __align__(8) uint64_t tma_bar;
     __shared__ int task_sh;
     __shared__ int flag_sh;
+    __shared__ int merge_sh[2];
     if (threadIdx.x == 0) mbar_init(&tma_bar, 1);
     __syncthreads();
     uint32_t parity = 0;
@@ -699,7 +715,7 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
         }
         const FrameDesc f = L.frames ? L.frames[fi] : L.single;
         const bool border = f.nstrips > 1 || f.wrap;
-        // [borders merged, ready, arrivals at border 0, 1, ...]
+        // [borders merged, (unused), arrivals at border 0, 1, ...]
         int* done_ctr = L.counters + kCtrFrames + kCtrPerFrame * fi;
 
         if (kind == kTaskP1) {
@@ -726,37 +742,42 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
             if (s.bulk) parity ^= 1u;
             phase1(s, sm);
             if (border) {
-                // arrive at the (up to two) borders of this strip; the second arrival at a
-                // border merges it, and the last merged border makes the frame ready
+                // arrive at the (up to two) borders of this strip (both arrivals at once,
+                // by two threads); the second arrival at a border merges it.  A merged
+                // border adds one to the frame's count with a release reduction, and the
+                // frame is ready for P3 when the count reaches its number of borders.
                 const int n = f.nstrips;
                 const int nb = f.wrap ? n : n - 1;
                 __threadfence();
                 __syncthreads();
-                for (int side = 0; side < 2; ++side) {
+                if ((threadIdx.x & 31) == 0 && threadIdx.x < 64) {
+                    const int side = threadIdx.x >> 5;
                     const int b = side == 0 ? si : si - 1;  // right border, then left border
                     const int bb = b < 0 ? (f.wrap ? n - 1 : -1) : b;
-                    if (bb < 0 || bb >= nb || (side == 1 && n == 1)) continue;  // uniform
-                    if (threadIdx.x == 0) {
+                    int mine = 0;
+                    if (bb >= 0 && bb < nb && !(side == 1 && n == 1)) {
                         const int need = n == 1 ? 1 : 2;
-                        flag_sh = atomicAdd(done_ctr + 2 + bb, 1) == need - 1;
+                        mine = atomicAdd(done_ctr + 2 + bb, 1) == need - 1 ? bb + 1 : 0;
                     }
+                    merge_sh[side] = mine;  // border + 1 to merge, 0 for none
+                }
+                __syncthreads();
+                for (int side = 0; side < 2; ++side) {
+                    const int bb = merge_sh[side] - 1;
+                    if (bb < 0) continue;  // uniform
+                    __threadfence();
+                    border_merge(f, bb);
+                    __threadfence();
                     __syncthreads();
-                    if (flag_sh) {
-                        __threadfence();
-                        border_merge(f, bb);
-                        __threadfence();
-                        __syncthreads();
-                        if (threadIdx.x == 0 && atomicAdd(done_ctr, 1) == nb - 1)
-                            st_release(done_ctr + 1, 1);
-                    }
-                    __syncthreads();
+                    if (threadIdx.x == 0) red_release_add(done_ctr, 1);
                 }
             }
         } else {
             if (threadIdx.x == 0) {
+                const int nb = f.wrap ? f.nstrips : f.nstrips - 1;
                 int it = 0;
                 flag_sh = 1;
-                while (ld_acquire(done_ctr + 1) == 0) {
+                while (ld_acquire(done_ctr) < nb) {
                     __nanosleep(128);
                     if (++it > (1 << 24)) {  // ~2 s: give up and leave the strip alone,
                         report_timeout(f.status);  // its labels may not be written yet

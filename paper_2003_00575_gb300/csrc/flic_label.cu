@@ -604,9 +604,17 @@ __device__ void border_merge(const FrameDesc& f, int b) {
 
 // P3: flatten one strip once its frame's forest is final.  A warp takes groups of four
 // 128-column row chunks and issues their loads before any find, so that the latency of
-// one load round trip covers four chunks; consecutive pixels usually share a
-// strip-local root, so each thread remembers its last lookup.
-__device__ void phase3_strip(const FrameDesc& f, int si) {
+// one load round trip covers four chunks.  The roots found are kept in a block-wide cache
+// in shared memory (label -> root, one 64-bit entry each, so a reader never sees half of
+// an update; a collision only costs a find), so each distinct label of the strip costs
+// about one find; in front of it each thread remembers its last lookup.
+__device__ __forceinline__ unsigned dynamic_smem_bytes() {
+    unsigned v;
+    asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(v));
+    return v;
+}
+
+__device__ void phase3_strip(const FrameDesc& f, int si, unsigned long long* cache) {
     constexpr int G = 4;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -616,6 +624,11 @@ __device__ void phase3_strip(const FrameDesc& f, int si) {
     const int limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
     const bool vec = ((f.cols & 3) == 0) && ((c0 & 3) == 0) &&
                      ((reinterpret_cast<uintptr_t>(f.labels) & 15) == 0);
+    // cache entries: a power of two, at most 1024, inside this launch's shared memory
+    unsigned cn = 1024;
+    while (cn > 1 && cn * 8 > dynamic_smem_bytes()) cn >>= 1;
+    for (unsigned i = threadIdx.x; i < cn; i += blockDim.x) cache[i] = ~0ull;
+    __syncthreads();
     const int nchunk = (W + 127) >> 7;
     const int items = f.rows * nchunk;
     int last_l = -1, last_root = -1;
@@ -648,9 +661,16 @@ __device__ void phase3_strip(const FrameDesc& f, int si) {
                 const int l = v[g][q];
                 if (l < 0) continue;
                 if (l != last_l) {
-                    int budget = limit;
-                    last_root = find_global(f.labels, l, budget, false);
-                    if (budget <= 0) report_timeout(f.status);
+                    const unsigned h = ((unsigned)l * 0x9E3779B1u) >> 22 & (cn - 1);
+                    const unsigned long long e = ((volatile unsigned long long*)cache)[h];
+                    if ((unsigned)(e >> 32) == (unsigned)l) {
+                        last_root = (int)(unsigned)e;
+                    } else {
+                        int budget = limit;
+                        last_root = find_global(f.labels, l, budget, false);
+                        if (budget <= 0) report_timeout(f.status);
+                        cache[h] = ((unsigned long long)(unsigned)l << 32) | (unsigned)last_root;
+                    }
                     last_l = l;
                 }
                 if (last_root != l) {
@@ -787,7 +807,7 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
                 }
             }
             __syncthreads();
-            if (flag_sh) phase3_strip(f, si);
+            if (flag_sh) phase3_strip(f, si, reinterpret_cast<unsigned long long*>(smem_raw));
         }
         __syncthreads();  // shared memory is reused by the next task
     }

@@ -35,6 +35,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -74,6 +75,20 @@ def parse_args():
     p.add_argument("--serve-seconds", type=float, default=3.0,
                    help="short serving sweep (0 = skip); the full sweep is serve.py")
     return p.parse_args()
+
+
+def host_cpu() -> str:
+    """Model of the host CPU (x86 and Arm report it under different names)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                name = line.split(":", 1)[1].strip()
+                if name and not name.isdigit():
+                    return name
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return platform.machine()
 
 
 def rank_first_seed(rank: int, frames: int) -> int:
@@ -219,7 +234,7 @@ def run_reference(args, world, rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "frames": len(frames), "impl_note": "CPU oracle"},
         "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "host_cpu": host_cpu()},
         "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "frames_per_s": round(args.steps / total, 2),
@@ -340,6 +355,18 @@ def main():
                 "peak_source": f"of {peak_kind} (MEASURED_PEAKS.json hbm_gbs, burst copy)",
                 "kernel": "flic_label_kernel",
                 "algorithmic_bytes_per_launch": BYTES_PER_PX * total_px}
+    # the ALU roof beside it: the edge test's 2S predicates per measurement, 6 fp32 ops each
+    # (sub, mul, mul, mul, add, compare), against one fp32 op per lane per cycle
+    # (128 lanes per SM, no FMA in the predicate) at the sampled maximum SM clock
+    ops = sum(int((f.range > 0).sum()) * 2 * f.skip * 6 for f in frames)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = nsm * 128 * clocks["sm_max_mhz"] * 1e6 / 1e9 if clocks["sm_max_mhz"] else None
+    alu_achieved = ops / mean_launch_s / 1e9
+    roofline["alu"] = {"bound": "alu", "achieved": round(alu_achieved, 1),
+                       "peak": round(alu_peak, 1) if alu_peak else None, "unit": "Gop/s",
+                       "frac": round(alu_achieved / alu_peak, 4) if alu_peak else None,
+                       "ops_per_launch": ops,
+                       "peak_source": f"derived: {nsm} SMs x 128 fp32 lanes x max SM clock"}
 
     # ---- per-frame launches: the same frames, one flic_label call each
     single_lat = []
@@ -449,10 +476,21 @@ def main():
         for f in frames:
             oracle.label(f.range, f.sensor.elevation, f.sensor.az_step, f.delta, f.skip)
         dt = time.perf_counter() - t0
+        ncores = os.cpu_count() or 1
         cpu = {"value": round(total_px / dt / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"all {len(frames)} c4 frames once ({total_px} px, {dt:.2f} s), "
-                         f"sequential C BFS labeller, 1 thread of {os.cpu_count()} host cores",
-               "frames_per_s": round(len(frames) / dt, 2)}
+                         f"sequential C BFS labeller, 1 thread of {ncores} host cores",
+               "frames_per_s": round(len(frames) / dt, 2), "host_cpu": host_cpu()}
+        # the same frames spread over every host core (threads: the C labeller runs
+        # outside the interpreter lock)
+        from concurrent.futures import ThreadPoolExecutor
+        t0 = time.perf_counter()
+        with ThreadPoolExecutor(ncores) as ex:
+            list(ex.map(lambda f: oracle.label(f.range, f.sensor.elevation, f.sensor.az_step,
+                                               f.delta, f.skip), frames))
+        dt_all = time.perf_counter() - t0
+        cpu["all_cores"] = {"value": round(total_px / dt_all / 1e6, 3), "unit": UNIT,
+                            "cores": ncores, "frames_per_s": round(len(frames) / dt_all, 2)}
 
     for h in handles:
         st = flic.flic_device_status(h)

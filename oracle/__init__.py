@@ -14,6 +14,8 @@ Functions and the passages they follow:
   flips       FP64 Eq. 2 decision vs the fp32 one
   project     spherical projection of xyz into the range image (§I)
   scatter     labels back to points (§I, Fig. 1)
+  filter_relabel  cluster candidates: components below a minimum size dropped, the rest
+              numbered by their minimum index (§III-B, the minimum of 100 points)
 """
 from __future__ import annotations
 
@@ -182,3 +184,27 @@ def scatter(labels, point_pixel):
     out = np.empty(pix.shape[0], np.int32)
     _load().oracle_scatter(_ptr(lab), _ptr(pix), pix.shape[0], _ptr(out))
     return out
+
+
+def filter_relabel(labels, min_size: int):
+    """Cluster candidates (§III-B: labelled clusters with fewer than a minimum number of
+    measurements are discarded as noise; the paper uses 100).  ``labels`` is the output of
+    ``label`` (each measurement carries the minimum index of its component, -1 elsewhere).
+    Components with fewer than ``min_size`` pixels are dropped (their pixels become -1);
+    the others are numbered 0..N-1 in ascending order of their minimum index, i.e. in the
+    raster order of their first pixel.  Returns (int32 labels of the same shape, N).
+
+    The plain definition: a histogram of the labels (np.bincount), the kept minima in
+    ascending order (np.flatnonzero), each pixel mapped to the rank of its minimum."""
+    lab = np.asarray(labels).astype(np.int64)
+    flat = lab.reshape(-1)
+    out = np.full(flat.shape, -1, np.int32)
+    v = flat >= 0
+    if not v.any():
+        return out.reshape(lab.shape), 0
+    counts = np.bincount(flat[v], minlength=flat.size)
+    kept = np.flatnonzero((counts > 0) & (counts >= min_size))
+    ids = np.full(flat.size, -1, np.int64)
+    ids[kept] = np.arange(kept.size)
+    out[v] = ids[flat[v]]
+    return out.reshape(lab.shape), int(kept.size)

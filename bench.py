@@ -368,6 +368,28 @@ def main():
                        "ops_per_launch": ops,
                        "peak_source": f"derived: {nsm} SMs x 128 fp32 lanes x max SM clock"}
 
+    # ---- cluster candidates (§III-B, the paper's minimum of 100 points) over the batch's
+    # fresh labels: flic_filter_relabel_batch alone is timed
+    rl_ms = []
+    rl_num = torch.empty(len(frames), dtype=torch.int32, device=dev)
+    rl_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for rep in range(23):
+        k = rep % NCOPIES
+        flic.flic_label_batch(batches[k], bargs[k], stream)
+        rl_ev[0].record(stream)
+        flic.flic_filter_relabel_batch(batches[k], bargs[k], 100, rl_num, stream)
+        rl_ev[1].record(stream)
+        torch.cuda.synchronize()
+        if rep >= 3:
+            rl_ms.append(rl_ev[0].elapsed_time(rl_ev[1]))
+    cluster_filter = {
+        "min_size": 100, "ms_per_batch": round(statistics.median(rl_ms), 4),
+        "mpixel_per_s": round(total_px / (statistics.median(rl_ms) / 1e3) / 1e6, 1),
+        "kept_clusters_per_frame": round(float(rl_num.float().mean().item()), 2),
+        "launches": 6,
+        "note": "relabel of the c4 batch's labels: components under 100 px dropped, the rest "
+                "numbered 0..N-1 by minimum index; timed alone, after a fresh labelling"}
+
     # ---- per-frame launches: the same frames, one flic_label call each
     single_lat = []
     pf_total = []
@@ -517,6 +539,7 @@ def main():
             "e2e": e2e,
             "roofline": roofline,
             "projection": projection,
+            "cluster_filter": cluster_filter,
             "serving": serving,
             "cpu_baseline": cpu,
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},

@@ -234,9 +234,42 @@ flic_status flic_plan_frame(int32_t rows, int32_t cols, int32_t skip, int32_t px
 flic_status flic_batch_last_plan(flic_batch b, int32_t* info);
 
 /*
+ * flic_filter_relabel — cluster candidates (§III-B: labelled clusters with fewer than a
+ * minimum number of measurements are discarded as sensor noise; the paper's minimum is
+ * 100 points).  In place, on labels produced by flic_label / flic_label_batch for this
+ * handle's frame shape (component minima, -1 where no measurement): every component with
+ * fewer than min_size pixels becomes -1, and the others are numbered 0..N-1 in ascending
+ * order of their minimum index, i.e. in the raster order of their first pixels (the
+ * numbering of scipy.ndimage.label, minus one).
+ *   labels    device int32 rows*cols, read and rewritten
+ *   min_size  pixels a component needs to be kept (<= 1 keeps every component)
+ *   num_out   device int32 receiving N, or NULL
+ * Uses handle-owned scratch (8 bytes per pixel, allocated on the first call; the call
+ * then synchronises once).  Other labels (values outside 0..rows*cols-1) are left in
+ * place and reported by flic_device_status; values inside that range that are not
+ * component minima give an unspecified numbering.  Errors: FLIC_ERR_INVALID (NULL),
+ * FLIC_ERR_OOM, FLIC_ERR_CUDA.
+ */
+flic_status flic_filter_relabel(flic_handle h, int32_t* labels, int32_t min_size,
+                                int32_t* num_out, void* stream);
+
+/*
+ * flic_filter_relabel_batch — the same for nframes frames in one set of launches: frame i
+ * has hs[i]'s shape and labels[i] (device int32, rewritten in place); num_out is a device
+ * int32 array of nframes (N of each frame) or NULL.  Scratch (8 bytes per pixel of the
+ * batch) belongs to the batch object and grows on demand; growing waits for the batch's
+ * previous relabel.  Errors: FLIC_ERR_INVALID, FLIC_ERR_OOM, FLIC_ERR_CUDA.
+ */
+flic_status flic_filter_relabel_batch(flic_batch b, const flic_handle* hs,
+                                      int32_t* const* labels, int32_t nframes, int32_t min_size,
+                                      int32_t* num_out, void* stream);
+
+/*
  * flic_device_status — synchronise the device, read and (if clear != 0) reset the
- * handle's device error word.  Returns FLIC_OK or FLIC_ERR_TIMEOUT when a bounded loop
- * in a kernel gave up since the last reset (labels of that call are then not valid).
+ * handle's device error word.  Returns FLIC_OK; FLIC_ERR_TIMEOUT when a bounded loop in a
+ * kernel gave up since the last reset (labels of that call are then not valid); or
+ * FLIC_ERR_INVALID when flic_filter_relabel(_batch) met a label outside 0..rows*cols-1
+ * (such labels are left as they are and never used as an index).
  */
 flic_status flic_device_status(flic_handle h, int32_t clear);
 

@@ -18,7 +18,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libflic.so")
-SOURCES = ["flic_label.cu", "flic_project.cu", "flic_api.cu", "flic_noalloc.cu", "flic_serve.cu"]
+SOURCES = ["flic_label.cu", "flic_project.cu", "flic_relabel.cu", "flic_api.cu", "flic_noalloc.cu",
+           "flic_serve.cu"]
 HEADERS = ["flic_internal.h", "flic_device.cuh"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

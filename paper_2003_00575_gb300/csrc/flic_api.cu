@@ -136,6 +136,7 @@ struct flic_ctx {
     int32_t* d_srow = nullptr;
     float inv_az_step = 0.0f;
     unsigned long long* d_keys = nullptr;
+    int32_t* d_rl = nullptr;  // flic_filter_relabel scratch (relabel_scratch_ints)
     float* d_range = nullptr;
     int32_t* d_status = nullptr;
     int iter_limit = 0;
@@ -168,6 +169,17 @@ struct flic_batch_ctx {
     // the previous call's arguments and launch shape: an identical call replays the graph
     std::vector<const void*> last_args;
     cudaGraphExec_t last_exec = nullptr;
+    // flic_filter_relabel_batch: descriptors (pinned staging + device) and scratch
+    flic::RelabelFrame* h_rl = nullptr;
+    flic::RelabelFrame* d_rl = nullptr;
+    int32_t* d_rl_scratch = nullptr;
+    size_t rl_scratch_ints = 0;
+    int32_t* h_rl_tile_frame = nullptr;  // pinned: the frame of each tile
+    int32_t* d_rl_tile_frame = nullptr;
+    size_t rl_tiles = 0;
+    cudaEvent_t rl_staged = nullptr;  // descriptor upload done: staging reusable
+    cudaEvent_t rl_done = nullptr;    // last relabel done: descriptors and scratch reusable
+    bool rl_pending = false;
 };
 
 namespace {
@@ -268,6 +280,7 @@ void free_ctx(flic_ctx* h) {
     cudaFree(h->d_rowb);
     cudaFree(h->d_srow);
     cudaFree(h->d_keys);
+    cudaFree(h->d_rl);
     cudaFree(h->d_range);
     cudaFree(h->d_status);
     cudaFree(h->d_counters);
@@ -501,6 +514,8 @@ flic_status flic_device_status(flic_handle h, int32_t clear) {
             e = cudaMemset(h->d_counters, 0, sizeof(int32_t) * flic::counter_ints(1));
         if (e != cudaSuccess) return cuda_fail(e, "flic_device_status clear");
     }
+    if (v == flic::kRelabelBadLabel)
+        return fail(FLIC_ERR_INVALID, "flic_filter_relabel saw a label outside the frame");
     if (v != 0) return fail(FLIC_ERR_TIMEOUT, "a bounded device loop gave up (status %d)", v);
     return FLIC_OK;
 }
@@ -537,7 +552,12 @@ flic_status flic_batch_create(int32_t max_frames, flic_batch* out) {
         (e = cudaMalloc((void**)&b->d_dims, 2 * sizeof(int32_t))) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming)) != cudaSuccess ||
         (e = cudaEventCreateWithFlags(&b->kernel_done, cudaEventDisableTiming)) != cudaSuccess ||
-        (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        (e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaHostAlloc((void**)&b->h_rl, sizeof(flic::RelabelFrame) * (size_t)max_frames,
+                           cudaHostAllocDefault)) != cudaSuccess ||
+        (e = cudaMalloc((void**)&b->d_rl, sizeof(flic::RelabelFrame) * (size_t)max_frames)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->rl_staged, cudaEventDisableTiming)) != cudaSuccess ||
+        (e = cudaEventCreateWithFlags(&b->rl_done, cudaEventDisableTiming)) != cudaSuccess) {
         flic_batch_destroy(b);
         return cuda_fail(e, "flic_batch_create");
     }
@@ -569,6 +589,13 @@ flic_status flic_batch_destroy(flic_batch b) {
     cudaFree(b->d_counters);
     if (b->staged) cudaEventDestroy(b->staged);
     if (b->kernel_done) cudaEventDestroy(b->kernel_done);
+    if (b->h_rl) cudaFreeHost(b->h_rl);
+    cudaFree(b->d_rl);
+    cudaFree(b->d_rl_scratch);
+    cudaFree(b->d_rl_tile_frame);
+    if (b->h_rl_tile_frame) cudaFreeHost(b->h_rl_tile_frame);
+    if (b->rl_staged) cudaEventDestroy(b->rl_staged);
+    if (b->rl_done) cudaEventDestroy(b->rl_done);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     delete b;
     if (e != cudaSuccess) return cuda_fail(e, "flic_batch_destroy");
@@ -751,6 +778,114 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
     int info[8] = {ntasks, grid, t.max_strips, t.threads, (int)smem, total_strips, nframes,
                    resident};
     std::memcpy(b->last_info, info, sizeof(info));
+    return FLIC_OK;
+}
+
+namespace {
+
+// Carve a relabel scratch block: sizes (npix_all), root and kept bitmasks, tile arrays.
+void carve_relabel(flic::RelabelLaunch* L, int32_t* base, size_t npix_all, int ntiles) {
+    L->roots = reinterpret_cast<uint32_t*>(base + npix_all);
+    L->kept = L->roots + (size_t)ntiles * (flic::kRelabelTile / 32);
+    L->tile_cnt = reinterpret_cast<int32_t*>(L->kept + (size_t)ntiles * (flic::kRelabelTile / 32));
+    L->tile_off = L->tile_cnt + ntiles;
+}
+
+}  // namespace
+
+flic_status flic_filter_relabel(flic_handle h, int32_t* labels, int32_t min_size,
+                                int32_t* num_out, void* stream) {
+    if (!h) return fail(FLIC_ERR_INVALID, "NULL handle");
+    if (!labels) return fail(FLIC_ERR_INVALID, "NULL labels");
+    const int npix = h->R * h->C;
+    const int ntiles = (npix + flic::kRelabelTile - 1) / flic::kRelabelTile;
+    cudaError_t e;
+    if (!h->d_rl) {
+        const size_t ints = flic::relabel_scratch_ints((size_t)npix, (size_t)ntiles);
+        if ((e = cudaMalloc((void**)&h->d_rl, ints * sizeof(int32_t))) != cudaSuccess)
+            return cuda_fail(e, "relabel scratch");
+    }
+    flic::RelabelLaunch L{};
+    L.nframes = 1;
+    L.ntiles = ntiles;
+    L.min_size = min_size;
+    carve_relabel(&L, h->d_rl, (size_t)npix, ntiles);
+    L.single = {labels, h->d_rl, num_out, h->d_status, npix, 0};
+    e = flic::launch_relabel(L, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "flic_filter_relabel launch");
+    return FLIC_OK;
+}
+
+flic_status flic_filter_relabel_batch(flic_batch b, const flic_handle* hs,
+                                      int32_t* const* labels, int32_t nframes, int32_t min_size,
+                                      int32_t* num_out, void* stream) {
+    if (!b || !hs || !labels) return fail(FLIC_ERR_INVALID, "NULL argument");
+    if (nframes < 0 || nframes > b->max_frames)
+        return fail(FLIC_ERR_INVALID, "nframes must be 0..%d", b->max_frames);
+    if (nframes == 0) return FLIC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e;
+    size_t npix_all = 0;
+    int ntiles = 0;
+    for (int i = 0; i < nframes; ++i) {
+        if (!hs[i] || !labels[i]) return fail(FLIC_ERR_INVALID, "NULL handle or labels %d", i);
+        const int npix = hs[i]->R * hs[i]->C;
+        npix_all += (size_t)npix;
+        ntiles += (npix + flic::kRelabelTile - 1) / flic::kRelabelTile;
+    }
+    // the pinned staging may still be read by the previous upload, the scratch and the
+    // device descriptors by the previous launches
+    if (b->rl_pending && (e = cudaEventSynchronize(b->rl_staged)) != cudaSuccess)
+        return cuda_fail(e, "waiting for the previous upload");
+    const size_t need = flic::relabel_scratch_ints(npix_all, (size_t)ntiles);
+    if (need > b->rl_scratch_ints || (size_t)ntiles > b->rl_tiles) {
+        if (b->rl_pending && (e = cudaEventSynchronize(b->rl_done)) != cudaSuccess)
+            return cuda_fail(e, "waiting for the previous relabel");
+        cudaFree(b->d_rl_scratch);
+        cudaFree(b->d_rl_tile_frame);
+        cudaFreeHost(b->h_rl_tile_frame);
+        b->d_rl_scratch = nullptr;
+        b->d_rl_tile_frame = b->h_rl_tile_frame = nullptr;
+        b->rl_scratch_ints = b->rl_tiles = 0;
+        if ((e = cudaMalloc((void**)&b->d_rl_scratch, need * sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc((void**)&b->d_rl_tile_frame, ntiles * sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaHostAlloc((void**)&b->h_rl_tile_frame, ntiles * sizeof(int32_t),
+                               cudaHostAllocDefault)) != cudaSuccess)
+            return cuda_fail(e, "relabel scratch");
+        b->rl_scratch_ints = need;
+        b->rl_tiles = (size_t)ntiles;
+    }
+    int tile0 = 0;
+    size_t off = 0;
+    for (int i = 0; i < nframes; ++i) {
+        const int npix = hs[i]->R * hs[i]->C;
+        const int nt = (npix + flic::kRelabelTile - 1) / flic::kRelabelTile;
+        b->h_rl[i] = {labels[i], b->d_rl_scratch + off, num_out ? num_out + i : nullptr,
+                      hs[i]->d_status, npix, tile0};
+        for (int k = 0; k < nt; ++k) b->h_rl_tile_frame[tile0 + k] = i;
+        off += (size_t)npix;
+        tile0 += nt;
+    }
+    if (b->rl_pending && (e = cudaStreamWaitEvent(st, b->rl_done, 0)) != cudaSuccess)
+        return cuda_fail(e, "stream wait");
+    e = cudaMemcpyAsync(b->d_rl, b->h_rl, sizeof(flic::RelabelFrame) * nframes,
+                        cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_rl_tile_frame, b->h_rl_tile_frame, sizeof(int32_t) * ntiles,
+                            cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->rl_staged, st);
+    if (e != cudaSuccess) return cuda_fail(e, "descriptor upload");
+    b->rl_pending = true;
+    flic::RelabelLaunch L{};
+    L.frames = b->d_rl;
+    L.tile_frame = b->d_rl_tile_frame;
+    L.nframes = nframes;
+    L.ntiles = ntiles;
+    L.min_size = min_size;
+    carve_relabel(&L, b->d_rl_scratch, npix_all, ntiles);
+    e = flic::launch_relabel(L, st);
+    if (e != cudaSuccess) return cuda_fail(e, "flic_filter_relabel_batch launch");
+    if ((e = cudaEventRecord(b->rl_done, st)) != cudaSuccess) return cuda_fail(e, "event record");
     return FLIC_OK;
 }
 

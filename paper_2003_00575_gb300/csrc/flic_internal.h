@@ -79,6 +79,38 @@ inline size_t strip_smem_bytes(int rows, int pitch_log2, int width, int skip) {
 // kernel's static shared memory).
 constexpr size_t kMaxDynSmem = 227 * 1024 - 1024;
 
+// Cluster candidates (flic_relabel.cu): per frame, the labels to renumber in place and an
+// int32 scratch array of npix (component sizes at root pixels, then their new ids); tiles
+// of kRelabelTile pixels, numbered over all frames (frame f's first tile is tile0), each
+// with two bitmasks of kRelabelTile bits (roots, kept roots).
+constexpr int kRelabelTile = 4096;
+constexpr int32_t kRelabelBadLabel = 1;  // == FLIC_ERR_INVALID: a label >= npix was seen
+struct RelabelFrame {
+    int32_t* labels;
+    int32_t* cnt;
+    int32_t* num_out;   // device int32: kept components, or nullptr
+    int32_t* status;    // the handle's device status word
+    int32_t npix;       // <= 2^21
+    int32_t tile0;
+};
+struct RelabelLaunch {
+    const RelabelFrame* frames;  // device array, or nullptr: use `single`
+    const int32_t* tile_frame;   // device, ntiles: the frame of each tile (nullptr: frame 0)
+    int32_t nframes;
+    int32_t ntiles;
+    int32_t min_size;
+    int32_t* tile_cnt;  // ntiles
+    int32_t* tile_off;  // ntiles
+    uint32_t* roots;    // ntiles x kRelabelTile / 32
+    uint32_t* kept;     // ntiles x kRelabelTile / 32
+    RelabelFrame single;
+};
+// Scratch ints a relabel of these frames needs: sizes, two bitmasks, two tile arrays.
+inline size_t relabel_scratch_ints(size_t npix_all, size_t ntiles) {
+    return npix_all + 2 * ntiles * (kRelabelTile / 32) + 2 * ntiles;
+}
+cudaError_t launch_relabel(const RelabelLaunch& L, cudaStream_t stream);
+
 // Kernel launchers (flic_label.cu / flic_project.cu).  Return cudaGetLastError().
 cudaError_t launch_label(const LabelLaunch& L, int grid, int threads, size_t smem,
                          cudaStream_t stream);

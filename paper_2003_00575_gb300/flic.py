@@ -49,6 +49,8 @@ SIGNATURES = {
     "flic_project": (_I32, [_P, _P, _I64, _P, _P, _P]),
     "flic_range_buffer": (_P, [_P]),
     "flic_scatter": (_I32, [_P, _P, _P, _I64, _P, _P]),
+    "flic_filter_relabel": (_I32, [_P, _P, _I32, _P, _P]),
+    "flic_filter_relabel_batch": (_I32, [_P, _P, _P, _I32, _I32, _P, _P]),
     "flic_batch_create": (_I32, [_I32, _P]),
     "flic_label_batch": (_I32, [_P, _P, _P, _P, _I32, _P]),
     "flic_batch_destroy": (_I32, [_P]),
@@ -289,11 +291,29 @@ def flic_label_batch(b: Batch, args: BatchArgs, stream=None) -> None:
 
 
 def flic_device_status(h: Handle, clear: bool = True) -> int:
-    """FLIC_OK, or FLIC_ERR_TIMEOUT when a bounded device loop gave up."""
+    """FLIC_OK; FLIC_ERR_TIMEOUT when a bounded device loop gave up; FLIC_ERR_INVALID when
+    flic_filter_relabel met a label outside the frame."""
     st = _lib.flic_device_status(h.ptr, 1 if clear else 0)
-    if st not in (FLIC_OK, FLIC_ERR_TIMEOUT):
+    if st not in (FLIC_OK, FLIC_ERR_TIMEOUT, FLIC_ERR_INVALID):
         _check(st)
     return st
+
+
+def flic_filter_relabel(h: Handle, labels, min_size: int, num_out=None, stream=None) -> None:
+    """Cluster candidates: components below min_size pixels -> -1, the rest 0..N-1."""
+    _check(_lib.flic_filter_relabel(h.ptr, _dptr(labels, "int32", h.npix, "labels"),
+                                    int(min_size),
+                                    None if num_out is None else _dptr(num_out, "int32", 1, "num_out"),
+                                    _stream(stream)))
+
+
+def flic_filter_relabel_batch(b: Batch, args: BatchArgs, min_size: int, num_out=None,
+                              stream=None) -> None:
+    """flic_filter_relabel over the frames of args (their labels buffers) in one go."""
+    _check(_lib.flic_filter_relabel_batch(
+        b.ptr, args.hs, args.ls, args.n, int(min_size),
+        None if num_out is None else _dptr(num_out, "int32", args.n, "num_out"),
+        _stream(stream)))
 
 
 def flic_debug_set_iter_limit(h: Handle, limit: int) -> None:

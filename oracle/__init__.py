@@ -14,6 +14,8 @@ Functions and the passages they follow:
   flips       FP64 Eq. 2 decision vs the fp32 one
   project     spherical projection of xyz into the range image (§I)
   scatter     labels back to points (§I, Fig. 1)
+  ground      ground extraction by the angle to the reading above (§III-A, Eq. 1)
+  label_ground  labelling with the ground removed first (§III-A before §III-B)
   filter_relabel  cluster candidates: components below a minimum size dropped, the rest
               numbered by their minimum index (§III-B, the minimum of 100 points)
 """
@@ -72,6 +74,8 @@ def _load():
         lib.oracle_project.restype = i32
         lib.oracle_scatter.argtypes = [P, P, i64, P]
         lib.oracle_scatter.restype = None
+        lib.oracle_ground.argtypes = [i32, i32, P, P, f64, f64, P]
+        lib.oracle_ground.restype = None
         _lib = lib
         return lib
 
@@ -208,3 +212,25 @@ def filter_relabel(labels, min_size: int):
     ids[kept] = np.arange(kept.size)
     out[v] = ids[flat[v]]
     return out.reshape(lab.shape), int(kept.size)
+
+
+def ground(range_img, elevation, theta: float, mount_height: float = 0.0):
+    """bool [rows, cols]: the readings §III-A removes as ground — spanning a horizontal
+    surface with the reading above (Eq. 1, tangent form; +-theta radians), the first row
+    deciding as the second; with mount_height > 0, horizontal readings above the line
+    z = rho tan(theta) - mount_height are kept (not ground)."""
+    rng = _f32(range_img)
+    R, C = rng.shape
+    elev = _f64(elevation)
+    mask = np.zeros((R, C), np.uint8)
+    _load().oracle_ground(R, C, _ptr(rng), _ptr(elev), float(theta), float(mount_height),
+                          _ptr(mask))
+    return mask.astype(bool)
+
+
+def label_ground(range_img, elevation, az_step: float, delta: float, skip: int, wrap: bool,
+                 theta: float, mount_height: float = 0.0):
+    """Labels with the ground removed first: ground readings become non-measurements."""
+    rng = _f32(range_img)
+    g = ground(rng, elevation, theta, mount_height)
+    return label(np.where(g, np.float32(0), rng), elevation, az_step, delta, skip, wrap)

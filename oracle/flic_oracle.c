@@ -19,6 +19,8 @@
  *   oracle_flips      FP64 decision of every candidate pair against the fp32 one
  *   oracle_project    spherical projection of xyz points into the range image (§I)
  *   oracle_scatter    labels back onto the points (§I, Fig. 1)
+ *   oracle_ground     ground extraction by the angle to the reading above (§III-A, Eq. 1
+ *                     in its tangent form), with the optional height-line exception
  */
 #include <float.h>
 #include <math.h>
@@ -398,4 +400,88 @@ done:
 /* Labels back onto the points (§I, Fig. 1: every point takes its pixel's instance). */
 void oracle_scatter(const int32_t* labels, const int32_t* pix, int64_t n, int32_t* point_labels) {
     for (int64_t i = 0; i < n; ++i) point_labels[i] = pix[i] >= 0 ? labels[pix[i]] : -1;
+}
+
+/*
+ * Ground extraction (§III-A).  Each reading d2 at (r, c) is compared with the reading d1
+ * above it (row r-1, the previous channel; rows are channels from the top), alpha being
+ * the angle between the two beams.  Eq. 1 gives the angle beta at the upper point between
+ * the ray back to the sensor and the segment to the lower point; its tangent form (Eq. 1
+ * simplified) needs sin(alpha) and cos(alpha) as pre-computed constants:
+ *     tan(beta) = d2 sin(alpha) / (d1 - d2 cos(alpha)).
+ * A horizontal surface gives beta = gamma = the depression angle of the upper beam
+ * (-elevation of row r-1); a reading spans a horizontal surface when beta lies within
+ * +-theta of gamma (the paper: 10 degrees).  Without the division:
+ *     num = d2 * sin_a, den = d1 - d2 * cos_a,
+ *     horizontal  <=>  den > 0  and  tan(gamma - theta) * den <= num <= tan(gamma + theta) * den
+ * (den <= 0 is beta >= 90 degrees; a bound at or past +-90 degrees is -inf / +inf), every
+ * operation one fp32 rounding.  The first channel has no channel above: it takes the
+ * decision of the second (the paper extends beta_2 to the first channel).  Both readings
+ * must be measurements.
+ * Height exception (mount_height > 0): a horizontal reading at height z = d sin(e) (from
+ * the sensor) above the line z = rho tan(theta) - mount_height (rho = d cos(e), the line
+ * from the wheels rising at the threshold slope) is kept.
+ * Tables, double then float, rows r = 1..R-1: sa, ca; tlo, thi; and for every row se, ce.
+ * mask[p] = 1 for ground.  theta <= 0: no ground.
+ */
+static int oracle_horizontal(float d1, float d2, float sa, float ca, float tlo, float thi) {
+    if (!oracle_valid(d1) || !oracle_valid(d2)) return 0;
+    const float num = d2 * sa;
+    const float t = d2 * ca;
+    const float den = d1 - t;
+    if (!(den > 0.0f)) return 0;
+    const float lo = tlo * den;
+    const float hi = thi * den;
+    return num >= lo && num <= hi;
+}
+
+void oracle_ground(int32_t R, int32_t C, const float* range, const double* elev, double theta,
+                   double mount_height, uint8_t* mask) {
+    memset(mask, 0, (size_t)R * C);
+    if (!(theta > 0.0) || R < 2) return;
+    const double half_pi = 2.0 * atan(1.0);
+    float* sa = (float*)calloc((size_t)R, sizeof(float));
+    float* ca = (float*)calloc((size_t)R, sizeof(float));
+    float* tlo = (float*)calloc((size_t)R, sizeof(float));
+    float* thi = (float*)calloc((size_t)R, sizeof(float));
+    float* se = (float*)calloc((size_t)R, sizeof(float));
+    float* ce = (float*)calloc((size_t)R, sizeof(float));
+    if (!sa || !ca || !tlo || !thi || !se || !ce) goto done;
+    for (int32_t r = 0; r < R; ++r) {
+        se[r] = (float)sin(elev[r]);
+        ce[r] = (float)cos(elev[r]);
+        if (r == 0) continue;
+        const double alpha = fabs(elev[r - 1] - elev[r]);
+        const double gamma = -elev[r - 1];
+        sa[r] = (float)sin(alpha);
+        ca[r] = (float)cos(alpha);
+        tlo[r] = gamma - theta <= -half_pi ? -INFINITY : (float)tan(gamma - theta);
+        thi[r] = gamma + theta >= half_pi ? INFINITY : (float)tan(gamma + theta);
+    }
+    const float tth = (float)tan(theta);
+    const float h = (float)mount_height;
+    for (int32_t r = 0; r < R; ++r) {
+        const int32_t rt = r == 0 ? 1 : r; /* the row whose test decides */
+        for (int32_t c = 0; c < C; ++c) {
+            const float d = range[(size_t)r * C + c];
+            if (!oracle_valid(d)) continue;
+            const float d1 = range[(size_t)(rt - 1) * C + c];
+            const float d2 = range[(size_t)rt * C + c];
+            if (!oracle_horizontal(d1, d2, sa[rt], ca[rt], tlo[rt], thi[rt])) continue;
+            if (mount_height > 0.0) {
+                const float z = d * se[r];
+                const float rho = d * ce[r];
+                const float line = rho * tth;
+                if (z > line - h) continue; /* above the height line: kept */
+            }
+            mask[(size_t)r * C + c] = 1;
+        }
+    }
+done:
+    free(sa);
+    free(ca);
+    free(tlo);
+    free(thi);
+    free(se);
+    free(ce);
 }

@@ -234,6 +234,22 @@ flic_status flic_plan_frame(int32_t rows, int32_t cols, int32_t skip, int32_t px
 flic_status flic_batch_last_plan(flic_batch b, int32_t* info);
 
 /*
+ * flic_set_ground — ground extraction (§III-A) before labelling, for this handle's
+ * flic_label, flic_label_batch and flic_edges calls and its served frames: a reading that
+ * spans a horizontal surface with the reading above it (row r-1, the previous channel) —
+ * the angle beta of Eq. 1 within +-theta of the upper beam's depression angle, tested in
+ * Eq. 1's tangent form with per-row constants, den > 0 and
+ * tan(gamma - theta)*den <= d2*sin(alpha) <= tan(gamma + theta)*den — counts as no
+ * measurement (label -1, no edges).  The first row decides as the second.  With
+ * mount_height > 0 (metres from the sensor down to the wheels' contact plane), horizontal
+ * readings above the line z = rho*tan(theta) - mount_height are kept (raised surfaces such
+ * as car roofs, §III-A's height image).  theta in radians (the paper uses 10 degrees);
+ * theta <= 0 turns it off.  Synchronises (the table is uploaded).  Errors:
+ * FLIC_ERR_INVALID (theta >= 90 degrees or not finite), FLIC_ERR_OOM, FLIC_ERR_CUDA.
+ */
+flic_status flic_set_ground(flic_handle h, double theta, double mount_height);
+
+/*
  * flic_filter_relabel — cluster candidates (§III-B: labelled clusters with fewer than a
  * minimum number of measurements are discarded as sensor noise; the paper's minimum is
  * 100 points).  In place, on labels produced by flic_label / flic_label_batch for this

@@ -137,6 +137,9 @@ struct flic_ctx {
     float inv_az_step = 0.0f;
     unsigned long long* d_keys = nullptr;
     int32_t* d_rl = nullptr;  // flic_filter_relabel scratch (relabel_scratch_ints)
+    float* d_gnd = nullptr;   // ground table (flic_set_ground), nullptr: off
+    float gnd_tan = 0.0f, gnd_height = 0.0f;
+    double gnd_theta_arg = 0.0, gnd_height_arg = 0.0;  // the flic_set_ground arguments
     float* d_range = nullptr;
     int32_t* d_status = nullptr;
     int iter_limit = 0;
@@ -203,6 +206,9 @@ flic::FrameDesc frame_desc(const flic_ctx* h, const float* range, int32_t* label
     f.strip_w = pl.strip_w;
     f.pitch_log2 = pl.pitch_log2;
     f.iter_limit = h->iter_limit;
+    f.gnd = h->d_gnd;
+    f.gnd_tan = h->gnd_tan;
+    f.gnd_height = h->gnd_height;
     return f;
 }
 
@@ -281,6 +287,7 @@ void free_ctx(flic_ctx* h) {
     cudaFree(h->d_srow);
     cudaFree(h->d_keys);
     cudaFree(h->d_rl);
+    cudaFree(h->d_gnd);
     cudaFree(h->d_range);
     cudaFree(h->d_status);
     cudaFree(h->d_counters);
@@ -517,6 +524,55 @@ flic_status flic_device_status(flic_handle h, int32_t clear) {
     if (v == flic::kRelabelBadLabel)
         return fail(FLIC_ERR_INVALID, "flic_filter_relabel saw a label outside the frame");
     if (v != 0) return fail(FLIC_ERR_TIMEOUT, "a bounded device loop gave up (status %d)", v);
+    return FLIC_OK;
+}
+
+flic_status flic_set_ground(flic_handle h, double theta, double mount_height) {
+    if (!h) return fail(FLIC_ERR_INVALID, "NULL handle");
+    if (!std::isfinite(theta) || !std::isfinite(mount_height) || theta >= 1.5707963267948966)
+        return fail(FLIC_ERR_INVALID, "theta must be finite and below 90 degrees");
+    cudaError_t e;
+    if (!(theta > 0.0) || h->R < 2) {  // off
+        if (h->d_gnd) {
+            if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "flic_set_ground");
+            cudaFree(h->d_gnd);
+            h->d_gnd = nullptr;
+        }
+        h->gnd_tan = h->gnd_height = 0.0f;
+        h->gnd_theta_arg = h->gnd_height_arg = 0.0;
+        ++h->version;
+        return FLIC_OK;
+    }
+    // per row, in double and rounded once: the constants of Eq. 1's tangent form and the
+    // bounds tan(gamma -+ theta) of a horizontal surface, gamma = the upper beam's
+    // depression angle
+    const double half_pi = 1.5707963267948966;
+    std::vector<float> t((size_t)h->R * flic::kGroundFields, 0.0f);
+    for (int r = 0; r < h->R; ++r) {
+        float* row = t.data() + (size_t)r * flic::kGroundFields;
+        row[4] = (float)std::sin(h->elev[r]);
+        row[5] = (float)std::cos(h->elev[r]);
+        if (r == 0) continue;
+        const double alpha = std::fabs(h->elev[r - 1] - h->elev[r]);
+        const double gamma = -h->elev[r - 1];
+        row[0] = (float)std::sin(alpha);
+        row[1] = (float)std::cos(alpha);
+        row[2] = gamma - theta <= -half_pi ? -INFINITY : (float)std::tan(gamma - theta);
+        row[3] = gamma + theta >= half_pi ? INFINITY : (float)std::tan(gamma + theta);
+    }
+    if (h->d_gnd) {  // a launch in flight may still read the old table
+        if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "flic_set_ground");
+    } else if ((e = cudaMalloc((void**)&h->d_gnd, t.size() * sizeof(float))) != cudaSuccess) {
+        return cuda_fail(e, "ground table");
+    }
+    if ((e = cudaMemcpy(h->d_gnd, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
+        cudaSuccess)
+        return cuda_fail(e, "ground table upload");
+    h->gnd_tan = (float)std::tan(theta);
+    h->gnd_height = mount_height > 0.0 ? (float)mount_height : 0.0f;
+    h->gnd_theta_arg = theta;
+    h->gnd_height_arg = mount_height;
+    ++h->version;
     return FLIC_OK;
 }
 
@@ -900,6 +956,7 @@ flic_status flic::clone_handle(flic_handle h, flic_handle* out, int* rows, int* 
     if (st == FLIC_OK) {
         (*out)->tune = h->tune;
         replan(*out);
+        if (h->d_gnd) st = flic_set_ground(*out, h->gnd_theta_arg, h->gnd_height_arg);
     }
     return st;
 }

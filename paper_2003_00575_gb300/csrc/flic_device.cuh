@@ -49,6 +49,42 @@ __device__ __forceinline__ void edge_d2_pair(float a, float b0, float b1, float 
     asm("mov.b64 {%0, %1}, %2;" : "=f"(d0), "=f"(d1) : "l"(d2));
 }
 
+// ---- ground extraction (§III-A) ---------------------------------------------------------
+// d2 spans a horizontal surface with the reading d1 above it when the angle beta of Eq. 1
+// (tangent form, the constants of the table row g) lies within the row's bounds:
+// num = d2 sin(alpha), den = d1 - d2 cos(alpha), den > 0 and lo*den <= num <= hi*den, every
+// operation one fp32 rounding.  Both readings must be measurements (0 for none).
+__device__ __forceinline__ bool ground_horizontal(float d1, float d2, const float* g) {
+    if (!(d1 > 0.0f) || !(d2 > 0.0f)) return false;
+    const float num = __fmul_rn(d2, __ldg(g + 0));
+    const float den = __fsub_rn(d1, __fmul_rn(d2, __ldg(g + 1)));
+    if (!(den > 0.0f)) return false;
+    return num >= __fmul_rn(__ldg(g + 2), den) && num <= __fmul_rn(__ldg(g + 3), den);
+}
+
+// A horizontal reading d of a row with table row g is kept (not ground) when it lies above
+// the height line z = rho tan(theta) - height (z = d sin(e), rho = d cos(e)).
+__device__ __forceinline__ bool ground_above_line(float d, const float* g, float tan_theta,
+                                                  float height) {
+    if (!(height > 0.0f)) return false;
+    const float z = __fmul_rn(d, __ldg(g + 4));
+    const float rho = __fmul_rn(d, __ldg(g + 5));
+    return z > __fsub_rn(__fmul_rn(rho, tan_theta), height);
+}
+
+// A reading of the frame from global memory, 0 where it is no measurement or ground.
+// The first row decides as the second (it has no row above).
+__device__ __forceinline__ float load_range_g(const FrameDesc& f, int r, int col) {
+    const float d = load_range(f.range + (size_t)r * f.cols + col);
+    if (!f.gnd || !(d > 0.0f) || f.rows < 2) return d;
+    const int rt = r == 0 ? 1 : r;
+    const float d1 = load_range(f.range + (size_t)(rt - 1) * f.cols + col);
+    const float d2 = rt == r ? d : load_range(f.range + (size_t)rt * f.cols + col);
+    if (!ground_horizontal(d1, d2, f.gnd + rt * kGroundFields)) return d;
+    if (ground_above_line(d, f.gnd + r * kGroundFields, f.gnd_tan, f.gnd_height)) return d;
+    return 0.0f;
+}
+
 __device__ __forceinline__ void report_timeout(int32_t* status) {
     if (status) atomicExch(status, kStatusTimeout);
 }

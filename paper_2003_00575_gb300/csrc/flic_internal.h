@@ -30,7 +30,14 @@ struct FrameDesc {
     int32_t pitch_log2;   // local row pitch of the shared-memory forest = 1 << pitch_log2
     int32_t iter_limit;   // bound of every device loop; 0 -> kDefaultIterLimit
     int32_t pad_;
+    // ground extraction (flic_set_ground), nullptr: off.  Row r: [0] sin, [1] cos of the
+    // angle to row r-1, [2] tan(gamma - theta), [3] tan(gamma + theta) (gamma = -elevation
+    // of row r-1, +-inf past +-90 degrees), [4] sin, [5] cos of row r's elevation.
+    const float* gnd;
+    float gnd_tan;        // tan(theta), for the height line
+    float gnd_height;     // mount height (m); <= 0: no height exception
 };
+constexpr int kGroundFields = 8;  // floats per row of the ground table (6 used)
 
 // One queue entry: P1 (stage, edges, strip-local labels) or P3 (flatten) of one strip.
 constexpr int32_t kTaskP1 = 0;

@@ -72,6 +72,8 @@ struct Strip {
     int RP;        // row pitch of the staged readings (>= W + S, multiple of 4)
     bool bulk;     // rows are 16-byte aligned: stage with TMA bulk copies
     int limit;
+    const float* gnd;  // ground table, nullptr: no ground extraction
+    float gnd_tan, gnd_height;
 };
 
 // Shared-memory carve-up of one strip (byte offsets; see strip_smem_bytes on the host).
@@ -208,6 +210,49 @@ __device__ void phase1_stage(const Strip& s, const Carve& sm, uint64_t* bar, uin
         for (int r = warp; r < s.R; r += nwarps)
             for (int c = lane; c < s.W; c += 32)
                 sm.stage[r * s.RP + c] = __ldg(s.range + (size_t)r * s.C + s.c0 + c);
+    }
+    __syncthreads();
+}
+
+// 0b. Ground extraction (§III-A): readings that span a horizontal surface with the reading
+//     above them become non-measurements in the staged strip, before the edge test.  All
+//     decisions are taken first (ballot words, in the space the edge words take later),
+//     then applied, so that no decision reads a reading already cleared.  The first row
+//     decides as the second.
+__device__ void phase1_ground(const Strip& s, const Carve& sm) {
+    const int lane = threadIdx.x & 31;
+    const int warp = threadIdx.x >> 5;
+    const int nwarps = blockDim.x >> 5;
+    const int nsl = s.sh - 5;
+    unsigned* gw = sm.words;  // R x P/32 words
+    for (int r = warp; r < s.R; r += nwarps) {
+        const int rt = r == 0 ? 1 : r;
+        const float* up = sm.stage + (rt - 1) * s.RP;
+        const float* lo = sm.stage + rt * s.RP;
+        const float* own = sm.stage + r * s.RP;
+        for (int cs = 0; cs < s.W; cs += 32) {  // same trip count on every lane
+            const int c = cs + lane;
+            bool g = false;
+            if (c < s.W) {
+                const float d = own[c];
+                if (valid_range(d)) {
+                    const float d1 = up[c], d2 = lo[c];
+                    g = ground_horizontal(valid_range(d1) ? d1 : 0.0f, valid_range(d2) ? d2 : 0.0f,
+                                          s.gnd + rt * kGroundFields) &&
+                        !ground_above_line(d, s.gnd + r * kGroundFields, s.gnd_tan, s.gnd_height);
+                }
+            }
+            const unsigned w = __ballot_sync(kFull, g);
+            if (lane == 0) gw[(r << nsl) + (cs >> 5)] = w;
+        }
+    }
+    __syncthreads();
+    for (int r = warp; r < s.R; r += nwarps) {
+        float* own = sm.stage + r * s.RP;
+        for (int cs = 0; cs < s.W; cs += 32) {
+            const int c = cs + lane;
+            if (c < s.W && ((gw[(r << nsl) + (cs >> 5)] >> lane) & 1u)) own[c] = 0.0f;
+        }
     }
     __syncthreads();
 }
@@ -484,6 +529,7 @@ __device__ void phase1_strip(const Strip& s, const Carve& sm) {
 }
 
 __device__ void phase1(const Strip& s, const Carve& sm) {
+    if (s.gnd) phase1_ground(s, sm);
     switch (s.S) {
         case 1: phase1_strip<1>(s, sm); break;
         case 2: phase1_strip<2>(s, sm); break;
@@ -532,8 +578,8 @@ __device__ void border_merge_s(const FrameDesc& f, int b, int limit,
         const int r = (rb << 5) + lane;
         const bool ok = r < R && tc < C;
         const int row = (ok ? r : 0) * C;  // frames hold at most 2^21 pixels
-        const float av = ok ? load_range(f.range + row + first + j) : 0.0f;
-        const float dv = ok ? load_range(f.range + row + tc) : 0.0f;
+        const float av = ok ? load_range_g(f, r, first + j) : 0.0f;
+        const float dv = ok ? load_range_g(f, r, tc) : 0.0f;
         const int ga = ok ? __ldcg(f.labels + row + first + j) : 0;
         const int gb = ok ? __ldcg(f.labels + row + tc) : 0;
         const float K = __ldg(f.kh + (ok ? r : 0) * S + k - 1);
@@ -563,11 +609,11 @@ __device__ void border_merge_narrow(const FrameDesc& f, int limit) {
     const int R = f.rows, C = f.cols, S = f.skip;
     for (int t = threadIdx.x; t < R * C; t += blockDim.x) {
         const int r = t / C, c = t - r * C;
-        const float a = load_range(f.range + t);
+        const float a = load_range_g(f, r, c);
         if (!(a > 0.0f)) continue;
         for (int k = C - c; k <= S; ++k) {
             const int tc = (c + k) % C;
-            const float d = load_range(f.range + (size_t)r * C + tc);
+            const float d = load_range_g(f, r, tc);
             if (d > 0.0f && edge_pred(a, d, __ldg(f.kh + r * S + k - 1), f.delta2)) {
                 int budget = limit;
                 union_global(f.labels, __ldcg(f.labels + t), __ldcg(f.labels + (size_t)r * C + tc),
@@ -757,6 +803,9 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
             s.bulk = ((s.C & 3) == 0) && ((s.c0 & 3) == 0) && ((s.W & 3) == 0) &&
                      ((reinterpret_cast<uintptr_t>(s.range) & 15) == 0);
             s.limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
+            s.gnd = f.rows >= 2 ? f.gnd : nullptr;
+            s.gnd_tan = f.gnd_tan;
+            s.gnd_height = f.gnd_height;
             const Carve sm = carve(smem_raw, s);
             phase1_stage(s, sm, &tma_bar, parity);
             if (s.bulk) parity ^= 1u;
@@ -828,7 +877,7 @@ __global__ void flic_edges_kernel(const FrameDesc f, uint16_t* __restrict__ mask
     for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < N; p += gridDim.x * blockDim.x) {
         const int r = p / f.cols;
         const int c = p - r * f.cols;
-        const float a = load_range(f.range + p);
+        const float a = load_range_g(f, r, c);
         unsigned m = 0;
         if (a > 0.0f) {
             for (int k = 1; k <= f.skip; ++k) {
@@ -838,12 +887,12 @@ __global__ void flic_edges_kernel(const FrameDesc f, uint16_t* __restrict__ mask
                     if (f.wrap) cc %= f.cols; else has = false;
                 }
                 if (has) {
-                    const float b = load_range(f.range + (size_t)r * f.cols + cc);
+                    const float b = load_range_g(f, r, cc);
                     if (b > 0.0f && edge_pred(a, b, __ldg(f.kh + r * f.skip + k - 1), f.delta2))
                         m |= 1u << (k - 1);
                 }
                 if (r + k < f.rows) {
-                    const float b = load_range(f.range + p + (size_t)k * f.cols);
+                    const float b = load_range_g(f, r + k, c);
                     if (b > 0.0f && edge_pred(a, b, __ldg(f.kv + r * f.skip + k - 1), f.delta2))
                         m |= 1u << (8 + k - 1);
                 }

@@ -49,6 +49,7 @@ SIGNATURES = {
     "flic_project": (_I32, [_P, _P, _I64, _P, _P, _P]),
     "flic_range_buffer": (_P, [_P]),
     "flic_scatter": (_I32, [_P, _P, _P, _I64, _P, _P]),
+    "flic_set_ground": (_I32, [_P, _F64, _F64]),
     "flic_filter_relabel": (_I32, [_P, _P, _I32, _P, _P]),
     "flic_filter_relabel_batch": (_I32, [_P, _P, _P, _I32, _I32, _P, _P]),
     "flic_batch_create": (_I32, [_I32, _P]),
@@ -297,6 +298,11 @@ def flic_device_status(h: Handle, clear: bool = True) -> int:
     if st not in (FLIC_OK, FLIC_ERR_TIMEOUT, FLIC_ERR_INVALID):
         _check(st)
     return st
+
+
+def flic_set_ground(h: Handle, theta: float, mount_height: float = 0.0) -> None:
+    """Ground extraction before labelling (theta in radians, <= 0: off)."""
+    _check(_lib.flic_set_ground(h.ptr, float(theta), float(mount_height)))
 
 
 def flic_filter_relabel(h: Handle, labels, min_size: int, num_out=None, stream=None) -> None:

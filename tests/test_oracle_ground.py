@@ -112,3 +112,18 @@ def test_disabled_and_label_composition():
     b = oracle.label(np.where(mask, 0, rng).astype(np.float32), elev, 2 * math.pi / 40, 0.5, 2, True)
     assert np.array_equal(a, b)
     assert (a.reshape(12, 40)[mask] == -1).all()
+
+
+@pytest.mark.parametrize("name", ["c1", "c2", "c3"])
+def test_synthetic_ground_truth(name):
+    """On the ray-cast scenes, the readings removed are nearly all hits of the ground plane
+    (object id 0) and most ground hits are removed: the ones kept lack a usable reading
+    above (dropout, an object in front) or sit in noise."""
+    from paper_2003_00575_gb300 import synth
+    f = {"c1": synth.config_c1, "c2": synth.config_c2,
+         "c3": lambda: synth.config_c3(with_xyz=False)}[name]()
+    g = oracle.ground(f.range, f.sensor.elevation, math.radians(10), 1.7)
+    truth = (f.object_id == 0) & (f.range > 0)
+    precision = (g & truth).sum() / max(g.sum(), 1)
+    recall = (g & truth).sum() / max(truth.sum(), 1)
+    assert precision > 0.95 and recall > 0.6, (precision, recall)

@@ -7,7 +7,8 @@ contraction, fp64 where stated); this module compiles it with gcc and exposes it
 ctypes with numpy arrays.
 
 Functions and the passages they follow:
-  tables      Eq. 3 constants per row and offset (§III-B, §III-B-2)
+  tables      Eq. 3 constants per row and offset (§III-B, §III-B-2); optionally the
+              true angle between the rays of a row (exact_ray)
   pred        Eq. 2/3 squared distance against delta (§III-B)
   edges       per-pixel edge bits for offsets 1..S (§III-B-1 binary images, §III-B-2)
   label       BFS connected-component labelling, min-index labels (§III-B-1)
@@ -58,6 +59,8 @@ def _load():
         i32, i64, f32, f64 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float, ctypes.c_double
         lib.oracle_tables.argtypes = [i32, P, f64, i32, P, P]
         lib.oracle_tables.restype = None
+        lib.oracle_tables_ex.argtypes = [i32, P, f64, i32, i32, P, P]
+        lib.oracle_tables_ex.restype = None
         lib.oracle_pred.argtypes = [f32, f32, f32, f32]
         lib.oracle_pred.restype = i32
         lib.oracle_pred_paper_form.argtypes = [f32, f32, f32, f32]
@@ -92,13 +95,16 @@ def _f64(a) -> np.ndarray:
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
-def tables(elevation, az_step: float, skip: int):
-    """(Kv, Kh), each float32 [rows, skip]: 4 sin^2(alpha/2) per row and offset (Eq. 3)."""
+def tables(elevation, az_step: float, skip: int, exact_ray: bool = False):
+    """(Kv, Kh), each float32 [rows, skip]: 4 sin^2(alpha/2) per row and offset (Eq. 3).
+    exact_ray: the horizontal alpha is the true angle between the rays of a row k columns
+    apart (K = 4 cos^2(e) sin^2(k step / 2)) instead of k times the azimuth step."""
     elev = _f64(elevation)
     R = elev.shape[0]
     kv = np.zeros((R, skip), np.float32)
     kh = np.zeros((R, skip), np.float32)
-    _load().oracle_tables(R, _ptr(elev), float(az_step), skip, _ptr(kv), _ptr(kh))
+    _load().oracle_tables_ex(R, _ptr(elev), float(az_step), skip, int(bool(exact_ray)),
+                             _ptr(kv), _ptr(kh))
     return kv, kh
 
 
@@ -116,22 +122,24 @@ def pred_paper_form(a: float, b: float, C2: float, delta: float) -> bool:
                                                float(np.float32(C2)), float(d * d)))
 
 
-def edges(range_img, elevation, az_step: float, delta: float, skip: int, wrap: bool = True):
+def edges(range_img, elevation, az_step: float, delta: float, skip: int, wrap: bool = True,
+          exact_ray: bool = False):
     """uint16 [rows, cols] edge bits: bit k-1 horizontal (+k, wrap), bit 8+k-1 vertical (+k)."""
     rng = _f32(range_img)
     R, C = rng.shape
-    kv, kh = tables(elevation, az_step, skip)
+    kv, kh = tables(elevation, az_step, skip, exact_ray)
     mask = np.zeros((R, C), np.uint16)
     _load().oracle_edges(R, C, _ptr(rng), _ptr(kv), _ptr(kh), skip, float(np.float32(delta)),
                          int(bool(wrap)), _ptr(mask))
     return mask
 
 
-def label(range_img, elevation, az_step: float, delta: float, skip: int, wrap: bool = True):
+def label(range_img, elevation, az_step: float, delta: float, skip: int, wrap: bool = True,
+          exact_ray: bool = False):
     """int32 [rows, cols] labels: min linear index of the component, -1 for invalid."""
     rng = _f32(range_img)
     R, C = rng.shape
-    kv, kh = tables(elevation, az_step, skip)
+    kv, kh = tables(elevation, az_step, skip, exact_ray)
     out = np.empty((R, C), np.int32)
     n = _load().oracle_label(R, C, _ptr(rng), _ptr(kv), _ptr(kh), skip,
                              float(np.float32(delta)), int(bool(wrap)), _ptr(out))

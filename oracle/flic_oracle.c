@@ -39,8 +39,23 @@ static int oracle_valid(float x) { return x > 0.0f && x <= FLT_MAX; }
  * manufacturer (§III-B), the angle "adjusted to the given offset" (§III-B-2).
  * Kv[r*S + k-1] (0 when r+k >= R) and Kh[r*S + k-1], k = 1..S.
  */
+void oracle_tables_ex(int32_t R, const double* elev, double az_step, int32_t S, int32_t exact_ray,
+                      float* Kv, float* Kh);
+
 void oracle_tables(int32_t R, const double* elev, double az_step, int32_t S, float* Kv,
                    float* Kh) {
+    oracle_tables_ex(R, elev, az_step, S, 0, Kv, Kh);
+}
+
+/*
+ * exact_ray != 0: the horizontal angle is the true angle between the two rays of row r,
+ * k columns apart, instead of k times the azimuth step: cos(alpha) = cos^2(e) cos(k step)
+ * + sin^2(e), so K = 2 - 2 cos(alpha) = 4 cos^2(e) sin^2(k step / 2) (the paper takes the
+ * manufacturer's step as the angle, §III-B; this is the variant §III-B-2's "adjusting the
+ * angle to the given offset" allows for rays off the horizon).
+ */
+void oracle_tables_ex(int32_t R, const double* elev, double az_step, int32_t S, int32_t exact_ray,
+                      float* Kv, float* Kh) {
     for (int32_t r = 0; r < R; ++r) {
         for (int32_t k = 1; k <= S; ++k) {
             float kv = 0.0f;
@@ -51,8 +66,9 @@ void oracle_tables(int32_t R, const double* elev, double az_step, int32_t S, flo
             }
             double alpha_h = (double)k * az_step;
             double sh = sin(alpha_h / 2.0);
+            double ce = exact_ray ? cos(elev[r]) : 1.0;
             Kv[r * S + (k - 1)] = kv;
-            Kh[r * S + (k - 1)] = (float)(4.0 * sh * sh);
+            Kh[r * S + (k - 1)] = (float)(4.0 * ce * ce * sh * sh);
         }
     }
 }

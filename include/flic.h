@@ -69,6 +69,10 @@ typedef enum {
 
 /* flic_create_ex flags */
 #define FLIC_FLAG_NO_WRAP 0x1u  /* columns do not wrap (sensor covers < 360 deg azimuth) */
+/* horizontal Eq. 3 constants from the true angle between a row's rays k columns apart,
+ * cos(alpha) = cos^2(e) cos(k az_step) + sin^2(e), i.e. K = 4 cos^2(e) sin^2(k az_step / 2),
+ * instead of the paper's k * az_step (§III-B) */
+#define FLIC_FLAG_EXACT_RAY 0x2u
 
 /* Largest frame the labeller accepts: rows * cols <= FLIC_MAX_PIXELS, rows <= FLIC_MAX_ROWS.
  * A frame is split into at most 64 full-height column strips of at most 32768 (padded)

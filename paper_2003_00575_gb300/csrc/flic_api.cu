@@ -213,8 +213,8 @@ flic::FrameDesc frame_desc(const flic_ctx* h, const float* range, int32_t* label
 }
 
 // Eq. 3 constants, K = 4 sin^2(alpha/2) = 2 - 2 cos(alpha), in double, rounded once.
-void build_k_tables(int R, const double* elev, double az_step, int S, std::vector<float>& kv,
-                    std::vector<float>& kh) {
+void build_k_tables(int R, const double* elev, double az_step, int S, bool exact_ray,
+                    std::vector<float>& kv, std::vector<float>& kh) {
     kv.assign((size_t)R * S, 0.0f);
     kh.assign((size_t)R * S, 0.0f);
     for (int r = 0; r < R; ++r) {
@@ -225,10 +225,13 @@ void build_k_tables(int R, const double* elev, double az_step, int S, std::vecto
                 double s = std::sin(alpha / 2.0);
                 v = (float)(4.0 * s * s);
             }
+            // horizontal: k times the step (§III-B), or the true angle between the two
+            // rays of row r: 2 - 2 cos(alpha) = 4 cos^2(e) sin^2(k step / 2)
             double alpha_h = (double)k * az_step;
             double sh = std::sin(alpha_h / 2.0);
+            double ce = exact_ray ? std::cos(elev[r]) : 1.0;
             kv[(size_t)r * S + k - 1] = v;
-            kh[(size_t)r * S + k - 1] = (float)(4.0 * sh * sh);
+            kh[(size_t)r * S + k - 1] = (float)(4.0 * ce * ce * sh * sh);
         }
     }
 }
@@ -332,7 +335,8 @@ flic_status flic_create_ex(int32_t rows, int32_t cols, const double* elevation, 
     if (!(delta > 0.0f) || !std::isfinite(delta))
         return fail(FLIC_ERR_INVALID, "delta must be positive and finite");
     if (skip < 1 || skip > FLIC_MAX_SKIP) return fail(FLIC_ERR_INVALID, "skip must be 1..%d", FLIC_MAX_SKIP);
-    if (flags & ~FLIC_FLAG_NO_WRAP) return fail(FLIC_ERR_INVALID, "unknown flags 0x%x", flags);
+    if (flags & ~(FLIC_FLAG_NO_WRAP | FLIC_FLAG_EXACT_RAY))
+        return fail(FLIC_ERR_INVALID, "unknown flags 0x%x", flags);
 
     flic_ctx* h = new flic_ctx();
     h->R = rows;
@@ -351,7 +355,8 @@ flic_status flic_create_ex(int32_t rows, int32_t cols, const double* elevation, 
     cudaError_t e = flic::label_kernel_setup(std::min((size_t)device_max_smem() - 1024, flic::kMaxDynSmem));
     if (e != cudaSuccess) { free_ctx(h); return cuda_fail(e, "kernel attributes"); }
 
-    build_k_tables(rows, elevation, az_step, skip, h->h_kv, h->h_kh);
+    build_k_tables(rows, elevation, az_step, skip, (flags & FLIC_FLAG_EXACT_RAY) != 0, h->h_kv,
+                   h->h_kh);
     if ((st = upload(&h->d_kv, h->h_kv, "Kv table")) != FLIC_OK) { free_ctx(h); return st; }
     if ((st = upload(&h->d_kh, h->h_kh, "Kh table")) != FLIC_OK) { free_ctx(h); return st; }
     std::vector<int32_t> zero(1, 0);

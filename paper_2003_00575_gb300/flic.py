@@ -24,6 +24,7 @@ FLIC_ERR_TIMEOUT = 4
 FLIC_ERR_BUSY = 5
 FLIC_ERR_UNSUPPORTED = 6
 FLIC_FLAG_NO_WRAP = 1
+FLIC_FLAG_EXACT_RAY = 2
 FLIC_MAX_PIXELS = 1 << 21
 FLIC_MAX_ROWS = 512
 FLIC_MAX_SKIP = 8
@@ -155,12 +156,12 @@ def flic_abi_version() -> int:
 
 
 def flic_create(rows: int, cols: int, elevation, az_step: float, delta: float, skip: int,
-                wrap: bool = True) -> Handle:
+                wrap: bool = True, exact_ray: bool = False) -> Handle:
     elev = np.ascontiguousarray(elevation, dtype=np.float64)
     if elev.shape != (rows,):
         raise ValueError("elevation must have one entry per row")
     out = ctypes.c_void_p()
-    flags = 0 if wrap else FLIC_FLAG_NO_WRAP
+    flags = (0 if wrap else FLIC_FLAG_NO_WRAP) | (FLIC_FLAG_EXACT_RAY if exact_ray else 0)
     _check(_lib.flic_create_ex(rows, cols, elev.ctypes.data, float(az_step), float(delta), skip,
                                flags, ctypes.byref(out)))
     return Handle(out.value, rows, cols, skip, float(np.float32(delta)), wrap)

@@ -416,6 +416,32 @@ def main():
         "ground_fraction_of_pixels": round(removed / total_px, 4),
         "note": "c4 batch labelled with ground extraction in the same persistent launch"}
 
+    # ---- segmentation quality (§IV metrics) of the GPU labels on the ray-cast scenes,
+    # whose per-pixel object ids are the ground truth: IoU_mu and P_x over the instances of
+    # at least 100 px, with the ground removed by the ground truth or by §III-A's
+    # extraction, for the direct neighbourhood (S = 1) and with skip connections
+    from paper_2003_00575_gb300 import quality
+    seg = {}
+    for cname, fr in (("c2", synth.config_c2()), ("c3", synth.config_c3(with_xyz=False))):
+        R, C = fr.sensor.rows, fr.sensor.cols
+        gt = fr.object_id
+        for S in sorted({1, fr.skip}):
+            for mode in ("gt_ground_removed", "ground_extraction"):
+                hq = flic.flic_create(R, C, fr.sensor.elevation, fr.sensor.az_step, fr.delta, S)
+                rng_q = fr.range
+                if mode == "gt_ground_removed":
+                    rng_q = np.where(gt == 0, np.float32(0), fr.range).astype(np.float32)
+                else:
+                    flic.flic_set_ground(hq, math.radians(10.0), 1.7)
+                lab_q = torch.empty(R * C, dtype=torch.int32, device=dev)
+                flic.flic_label(hq, torch.from_numpy(np.ascontiguousarray(rng_q).reshape(-1)).to(dev),
+                                lab_q, stream)
+                torch.cuda.synchronize()
+                seg[f"{cname}_S{S}_{mode}"] = quality.scores(lab_q.cpu().numpy(), gt)
+                hq.close()
+    seg["note"] = ("§IV metrics against the ray caster's object ids (instances >= 100 px); "
+                   "the paper's own numbers are on SemanticKITTI, not comparable")
+
     # ---- per-frame launches: the same frames, one flic_label call each
     single_lat = []
     pf_total = []
@@ -567,6 +593,7 @@ def main():
             "projection": projection,
             "cluster_filter": cluster_filter,
             "ground_extraction": ground_extraction,
+            "segmentation_quality": seg,
             "serving": serving,
             "cpu_baseline": cpu,
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},

@@ -524,6 +524,7 @@ flic_status flic_device_status(flic_handle h, int32_t clear) {
         e = cudaMemcpy(h->d_status, &z, sizeof(z), cudaMemcpyHostToDevice);
         if (e == cudaSuccess)
             e = cudaMemset(h->d_counters, 0, sizeof(int32_t) * flic::counter_ints(1));
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();  // landed before any stream's work
         if (e != cudaSuccess) return cuda_fail(e, "flic_device_status clear");
     }
     if (v == flic::kRelabelBadLabel)
@@ -573,6 +574,9 @@ flic_status flic_set_ground(flic_handle h, double theta, double mount_height) {
     if ((e = cudaMemcpy(h->d_gnd, t.data(), t.size() * sizeof(float), cudaMemcpyHostToDevice)) !=
         cudaSuccess)
         return cuda_fail(e, "ground table upload");
+    // a copy from pageable memory may return before its DMA lands; work on other
+    // (non-blocking) streams must find the table complete
+    if ((e = cudaDeviceSynchronize()) != cudaSuccess) return cuda_fail(e, "ground table upload");
     h->gnd_tan = (float)std::tan(theta);
     h->gnd_height = mount_height > 0.0 ? (float)mount_height : 0.0f;
     h->gnd_theta_arg = theta;

@@ -109,3 +109,44 @@ def test_full_queue_refuses(flic):
     want = oracle.label(f.range, s.elevation, s.az_step, 0.5, 3).reshape(-1)
     for r in recs:
         np.testing.assert_array_equal(ys[r.tag].numpy(), want)
+
+
+def test_served_with_ground_extraction(flic):
+    """Sensors whose handles have ground extraction on: the server's per-slot copies of the
+    handles carry the setting, and every served frame (images and clouds) equals the
+    oracle with the ground removed."""
+    import math
+    theta = math.radians(10.0)
+    sensors = synth.c5_sensors()
+    handles = [flic.flic_create(s.rows, s.cols, s.elevation, s.az_step, 0.5, 3) for s in sensors]
+    for h in handles:
+        flic.flic_set_ground(h, theta, 1.7)
+    frames = [(i % 4, synth.c5_frame(sensors[i % 4], 7000 + i, as_cloud=(i // 4) % 2 == 1))
+              for i in range(16)]
+    srv = flic.flic_server_create(handles, [260_001] * 4, nstreams=2, max_batch=8,
+                                  mem_budget=256 << 20)
+    try:
+        outs = []
+        for i, (si, f) in enumerate(frames):
+            x = torch.from_numpy((f.range if f.xyz is None else f.xyz).reshape(-1)).pin_memory()
+            n = f.range.size if f.xyz is None else f.xyz.shape[0]
+            y = torch.full((n,), -77, dtype=torch.int32).pin_memory()
+            assert flic.flic_server_submit(srv, si, 0 if f.xyz is None else 1, x, y, i) == flic.FLIC_OK
+            outs.append((x, y))  # the input stays alive until the frame completes
+        flic.flic_server_drain(srv, 60.0)
+        recs = flic.flic_server_poll(srv)
+    finally:
+        srv.close()
+        for h in handles:
+            h.close()
+    assert sorted(r.tag for r in recs) == list(range(16)) and all(r.status == 0 for r in recs)
+    for (si, f), (_, y) in zip(frames, outs):
+        s = f.sensor
+        if f.xyz is None:
+            want = oracle.label_ground(f.range, s.elevation, s.az_step, 0.5, 3, True, theta, 1.7)
+            want = want.reshape(-1)
+        else:
+            r, pix, _ = oracle.project(f.xyz, s.rows, s.cols, s.elevation, s.az_step)
+            want = oracle.scatter(oracle.label_ground(r, s.elevation, s.az_step, 0.5, 3, True,
+                                                      theta, 1.7), pix)
+        np.testing.assert_array_equal(y.numpy(), want, err_msg=f.name)

@@ -17,7 +17,8 @@
  *     Pixel p = r * cols + c.
  *   - Every pointer named "device" is a CUDA device pointer (or managed memory)
  *     allocated by the caller; the caller owns it.  Pointers named "host" are
- *     ordinary host memory, read during the call only.
+ *     ordinary host memory, read during the call only, except for the host buffers of
+ *     flic_label_batch_host and flic_server_submit, which are copied asynchronously.
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *     Every compute call only enqueues work on that stream and returns; results are
  *     ready once the stream reaches that point.  Only the *_create / *_destroy calls
@@ -198,6 +199,39 @@ flic_status flic_batch_create(int32_t max_frames, flic_batch* out);
 flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* const* ranges,
                              int32_t* const* labels, int32_t nframes, void* stream);
 flic_status flic_batch_destroy(flic_batch b);
+
+/*
+ * flic_label_batch_host — flic_label_batch on frames held in host memory (no counterpart
+ * in the paper; the labels equal flic_label_batch's):
+ *   hs           host array of nframes handles, as for flic_label_batch
+ *   host_ranges  host, the frames' range images back to back: frame i (rows_i*cols_i
+ *                fp32, row-major) starts right after frame i-1
+ *   host_labels  host, int32, the same packed layout; written when the work queued by
+ *                this call has finished on `stream`
+ *   groups       0: built-in (4); otherwise 1..16 groups of consecutive frames of about
+ *                equal pixel counts (at most nframes): each group's upload, labelling and
+ *                download are queued on separate streams, so that one group's copies run
+ *                under another group's labelling and both copy directions run at once
+ *   flags        0, or FLIC_HOST_INPUT_READY: host_ranges already hold this call's
+ *                readings, so the uploads and the labelling need not wait for work queued
+ *                earlier on `stream`; a call's uploads then run under the previous call's
+ *                downloads.  Without it the whole call is ordered after that work.
+ *   stream       the end of the call (labels in host_labels) is ordered before later work
+ *                on it
+ *   Host memory should be page-locked (cudaHostAlloc or cudaHostRegister) for the copies
+ *   to overlap; pageable memory gives the same labels with serialised copies.  The object
+ *   keeps two sets of device copies, used by alternate calls (each as large as the
+ *   largest batch seen; growing them waits for all earlier calls of this kind), and one
+ *   internal batch object per group and set, with this object's tuning and schedule.
+ *   The host buffers must not be modified or freed until the work on `stream` has
+ *   finished.  flic_batch_last_plan does not report these calls.
+ *   Errors: INVALID (NULL argument, bad groups or flags, the buffers overlap), BUSY
+ *   (nframes > max_frames), OOM, CUDA; on an error, work queued before it may still run.
+ */
+#define FLIC_HOST_INPUT_READY 0x1u
+flic_status flic_label_batch_host(flic_batch b, const flic_handle* hs, int32_t nframes,
+                                  const float* host_ranges, int32_t* host_labels,
+                                  int32_t groups, uint32_t flags, void* stream);
 
 /*
  * Launch-shape tuning (no counterpart in the paper).  px_per_cta: target pixels per

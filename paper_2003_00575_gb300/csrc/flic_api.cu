@@ -44,6 +44,10 @@ struct Tuning {
     int p3_delay = 8;     // batch: P3 tasks this many waves of blocks after their frame
 };
 
+// flic_label_batch_host: groups of frames whose copies overlap the labelling of others
+constexpr int kDefaultHostGroups = 4;
+constexpr int kMaxHostGroups = 16;
+
 struct StripPlan {
     int nstrips = 0;
     int strip_w = 0;
@@ -183,6 +187,21 @@ struct flic_batch_ctx {
     cudaEvent_t rl_staged = nullptr;  // descriptor upload done: staging reusable
     cudaEvent_t rl_done = nullptr;    // last relabel done: descriptors and scratch reusable
     bool rl_pending = false;
+    // flic_label_batch_host: two sides used by alternate calls, each with device copies of
+    // the packed frames, one sub-batch per group of frames (each replays its own graph) and
+    // per-group events; copy-in, labelling and copy-out streams
+    struct HostSide {
+        float* d_range = nullptr;
+        int32_t* d_labels = nullptr;
+        std::vector<flic_batch_ctx*> subs;
+        std::vector<cudaEvent_t> ev_in, ev_lab;
+        cudaEvent_t ev_kend = nullptr;  // the side's last labelling done: d_range reusable
+        cudaEvent_t ev_dend = nullptr;  // the side's last download done: d_labels reusable
+    } side[2];
+    size_t host_px_cap = 0;
+    uint64_t host_calls = 0;
+    cudaStream_t s_in = nullptr, s_lab = nullptr, s_out = nullptr;
+    cudaEvent_t ev_start = nullptr;
 };
 
 namespace {
@@ -662,6 +681,19 @@ flic_status flic_batch_destroy(flic_batch b) {
     if (b->rl_staged) cudaEventDestroy(b->rl_staged);
     if (b->rl_done) cudaEventDestroy(b->rl_done);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (auto& sd : b->side) {
+        for (flic_batch_ctx* sub : sd.subs) flic_batch_destroy(sub);
+        cudaFree(sd.d_range);
+        cudaFree(sd.d_labels);
+        for (cudaEvent_t ev : sd.ev_in) cudaEventDestroy(ev);
+        for (cudaEvent_t ev : sd.ev_lab) cudaEventDestroy(ev);
+        if (sd.ev_kend) cudaEventDestroy(sd.ev_kend);
+        if (sd.ev_dend) cudaEventDestroy(sd.ev_dend);
+    }
+    if (b->ev_start) cudaEventDestroy(b->ev_start);
+    if (b->s_in) cudaStreamDestroy(b->s_in);
+    if (b->s_lab) cudaStreamDestroy(b->s_lab);
+    if (b->s_out) cudaStreamDestroy(b->s_out);
     delete b;
     if (e != cudaSuccess) return cuda_fail(e, "flic_batch_destroy");
     return FLIC_OK;
@@ -843,6 +875,174 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
     int info[8] = {ntasks, grid, t.max_strips, t.threads, (int)smem, total_strips, nframes,
                    resident};
     std::memcpy(b->last_info, info, sizeof(info));
+    return FLIC_OK;
+}
+
+// ------------------------------------------------------------------ batch from host memory
+
+namespace {
+
+bool same_tuning(const Tuning& a, const Tuning& c) {
+    return a.px_per_cta == c.px_per_cta && a.threads == c.threads &&
+           a.max_strips == c.max_strips && a.ctas_per_sm == c.ctas_per_sm &&
+           a.p3_delay == c.p3_delay;
+}
+
+// The sub-batch of group g on one side, able to hold n frames, with the parent's launch
+// shape.
+flic_status host_sub(flic_batch_ctx* b, std::vector<flic_batch_ctx*>& subs, int g, int n,
+                     flic_batch_ctx** out) {
+    flic_batch_ctx* sub = g < (int)subs.size() ? subs[g] : nullptr;
+    if (sub && sub->max_frames < n) {  // too small: replaced (rare; synchronises)
+        flic_batch_destroy(sub);
+        subs[g] = sub = nullptr;
+    }
+    if (!sub) {
+        flic_status st = flic_batch_create(std::max(n, 1), &sub);
+        if (st != FLIC_OK) return st;
+        if (g < (int)subs.size()) subs[g] = sub; else subs.push_back(sub);
+    }
+    if (!same_tuning(sub->tune, b->tune)) {
+        if (sub->pending) cudaEventSynchronize(sub->kernel_done);
+        sub->tune = b->tune;
+        clear_graphs(sub);
+    }
+    *out = sub;
+    return FLIC_OK;
+}
+
+cudaError_t make_events(std::vector<cudaEvent_t>& v, int n) {
+    while ((int)v.size() < n) {
+        cudaEvent_t ev = nullptr;
+        cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        v.push_back(ev);
+    }
+    return cudaSuccess;
+}
+
+}  // namespace
+
+flic_status flic_label_batch_host(flic_batch b, const flic_handle* hs, int32_t nframes,
+                                  const float* host_ranges, int32_t* host_labels,
+                                  int32_t groups, uint32_t flags, void* stream) {
+    if (!b) return fail(FLIC_ERR_INVALID, "NULL batch");
+    if (nframes < 0) return fail(FLIC_ERR_INVALID, "nframes < 0");
+    if (flags & ~(uint32_t)FLIC_HOST_INPUT_READY) return fail(FLIC_ERR_INVALID, "unknown flags");
+    if (nframes == 0) return FLIC_OK;
+    if (nframes > b->max_frames)
+        return fail(FLIC_ERR_BUSY, "%d frames > batch capacity %d", nframes, b->max_frames);
+    if (!hs || !host_ranges || !host_labels) return fail(FLIC_ERR_INVALID, "NULL argument");
+    if (groups < 0 || groups > kMaxHostGroups)
+        return fail(FLIC_ERR_INVALID, "groups must be 0..%d", kMaxHostGroups);
+    std::vector<size_t> off((size_t)nframes + 1, 0);
+    for (int i = 0; i < nframes; ++i) {
+        if (!hs[i]) return fail(FLIC_ERR_INVALID, "frame %d: NULL handle", i);
+        off[i + 1] = off[i] + (size_t)hs[i]->R * hs[i]->C;
+    }
+    const size_t total = off[nframes];
+    {
+        const uintptr_t r0 = (uintptr_t)host_ranges, l0 = (uintptr_t)host_labels;
+        if (r0 < l0 + 4 * total && l0 < r0 + 4 * total)
+            return fail(FLIC_ERR_INVALID, "host ranges overlap host labels");
+    }
+    // frame-aligned groups of about equal pixel counts, at least one frame each
+    const int K = std::min(groups ? groups : kDefaultHostGroups, nframes);
+    std::vector<int> first((size_t)K + 1, 0);
+    for (int g = 1; g < K; ++g) {
+        const size_t target = total * (size_t)g / (size_t)K;
+        int j = first[g - 1] + 1;
+        while (j < nframes - (K - g) && off[j] < target) ++j;
+        first[g] = j;
+    }
+    first[K] = nframes;
+
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!b->s_in) {
+        if ((e = cudaStreamCreateWithFlags(&b->s_in, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&b->s_lab, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&b->s_out, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&b->ev_start, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(e, "flic_label_batch_host streams");
+        for (auto& sd : b->side)
+            if ((e = cudaEventCreateWithFlags(&sd.ev_kend, cudaEventDisableTiming)) != cudaSuccess ||
+                (e = cudaEventCreateWithFlags(&sd.ev_dend, cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(e, "flic_label_batch_host events");
+    }
+    flic_batch_ctx::HostSide& sd = b->side[b->host_calls & 1];
+    if ((e = make_events(sd.ev_in, K)) != cudaSuccess || (e = make_events(sd.ev_lab, K)) != cudaSuccess)
+        return cuda_fail(e, "flic_label_batch_host events");
+    std::vector<flic_batch_ctx*> sub((size_t)K, nullptr);
+    for (int g = 0; g < K; ++g) {
+        flic_status s = host_sub(b, sd.subs, g, first[g + 1] - first[g], &sub[g]);
+        if (s != FLIC_OK) return s;
+    }
+    // device copies of the packed frames on both sides (grown after all earlier calls of
+    // this kind have finished)
+    if (total > b->host_px_cap) {
+        if ((e = cudaStreamSynchronize(b->s_out)) != cudaSuccess)
+            return cuda_fail(e, "waiting for the previous host batches");
+        b->host_px_cap = 0;
+        for (auto& side : b->side) {
+            cudaFree(side.d_range);
+            cudaFree(side.d_labels);
+            side.d_range = nullptr;
+            side.d_labels = nullptr;
+        }
+        for (auto& side : b->side)
+            if (cudaMalloc((void**)&side.d_range, 4 * total) != cudaSuccess ||
+                cudaMalloc((void**)&side.d_labels, 4 * total) != cudaSuccess) {
+                cudaGetLastError();
+                return fail(FLIC_ERR_OOM, "device copies of %zu pixels", total);
+            }
+        b->host_px_cap = total;
+    }
+
+    // this side's buffers: the uploads follow its previous labelling, the labelling its
+    // previous download; without FLIC_HOST_INPUT_READY both also follow `stream`
+    if ((e = cudaStreamWaitEvent(b->s_in, sd.ev_kend, 0)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(b->s_lab, sd.ev_dend, 0)) != cudaSuccess)
+        return cuda_fail(e, "stream ordering");
+    if (!(flags & FLIC_HOST_INPUT_READY) &&
+        ((e = cudaEventRecord(b->ev_start, st)) != cudaSuccess ||
+         (e = cudaStreamWaitEvent(b->s_in, b->ev_start, 0)) != cudaSuccess ||
+         (e = cudaStreamWaitEvent(b->s_lab, b->ev_start, 0)) != cudaSuccess))
+        return cuda_fail(e, "stream ordering");
+    // all uploads first, so that the copy stream never waits on the host
+    for (int g = 0; g < K; ++g) {
+        const size_t p0 = off[first[g]], n = off[first[g + 1]] - p0;
+        if ((e = cudaMemcpyAsync(sd.d_range + p0, host_ranges + p0, 4 * n,
+                                 cudaMemcpyHostToDevice, b->s_in)) != cudaSuccess ||
+            (e = cudaEventRecord(sd.ev_in[g], b->s_in)) != cudaSuccess)
+            return cuda_fail(e, "range upload");
+    }
+    std::vector<const float*> rp;
+    std::vector<int32_t*> lp;
+    for (int g = 0; g < K; ++g) {
+        const int f0 = first[g], nf = first[g + 1] - f0;
+        rp.resize(nf);
+        lp.resize(nf);
+        for (int i = 0; i < nf; ++i) {
+            rp[i] = sd.d_range + off[f0 + i];
+            lp[i] = sd.d_labels + off[f0 + i];
+        }
+        if ((e = cudaStreamWaitEvent(b->s_lab, sd.ev_in[g], 0)) != cudaSuccess)
+            return cuda_fail(e, "stream ordering");
+        flic_status s = flic_label_batch(sub[g], hs + f0, rp.data(), lp.data(), nf, b->s_lab);
+        if (s != FLIC_OK) return s;
+        const size_t p0 = off[f0], n = off[first[g + 1]] - p0;
+        if ((e = cudaEventRecord(sd.ev_lab[g], b->s_lab)) != cudaSuccess ||
+            (e = cudaStreamWaitEvent(b->s_out, sd.ev_lab[g], 0)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(host_labels + p0, sd.d_labels + p0, 4 * n,
+                                 cudaMemcpyDeviceToHost, b->s_out)) != cudaSuccess)
+            return cuda_fail(e, "label download");
+    }
+    if ((e = cudaEventRecord(sd.ev_kend, b->s_lab)) != cudaSuccess ||
+        (e = cudaEventRecord(sd.ev_dend, b->s_out)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(st, sd.ev_dend, 0)) != cudaSuccess)
+        return cuda_fail(e, "stream ordering");
+    ++b->host_calls;
     return FLIC_OK;
 }
 

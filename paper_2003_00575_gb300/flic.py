@@ -25,6 +25,7 @@ FLIC_ERR_BUSY = 5
 FLIC_ERR_UNSUPPORTED = 6
 FLIC_FLAG_NO_WRAP = 1
 FLIC_FLAG_EXACT_RAY = 2
+FLIC_HOST_INPUT_READY = 1
 FLIC_MAX_PIXELS = 1 << 21
 FLIC_MAX_ROWS = 512
 FLIC_MAX_SKIP = 8
@@ -55,6 +56,7 @@ SIGNATURES = {
     "flic_filter_relabel_batch": (_I32, [_P, _P, _P, _I32, _I32, _P, _P]),
     "flic_batch_create": (_I32, [_I32, _P]),
     "flic_label_batch": (_I32, [_P, _P, _P, _P, _I32, _P]),
+    "flic_label_batch_host": (_I32, [_P, _P, _I32, _P, _P, _I32, _U32, _P]),
     "flic_batch_destroy": (_I32, [_P]),
     "flic_set_tuning": (_I32, [_P, _I32, _I32, _I32]),
     "flic_batch_set_tuning": (_I32, [_P, _I32, _I32, _I32, _I32]),
@@ -290,6 +292,36 @@ class BatchArgs:
 
 def flic_label_batch(b: Batch, args: BatchArgs, stream=None) -> None:
     _check(_lib.flic_label_batch(b.ptr, args.hs, args.rs, args.ls, args.n, _stream(stream)))
+
+
+def _hptr(t, dtype_name: str, numel: int, what: str) -> int:
+    """Host pointer of a contiguous CPU tensor (or numpy array) of the given dtype and size."""
+    if isinstance(t, np.ndarray):
+        if t.dtype != np.dtype(dtype_name) or not t.flags.c_contiguous or t.size != numel:
+            raise ValueError(f"{what} must be a contiguous {dtype_name} array of {numel} elements")
+        return t.ctypes.data
+    if t.is_cuda:
+        raise ValueError(f"{what} must be in host memory")
+    if str(t.dtype) != f"torch.{dtype_name}" or not t.is_contiguous() or t.numel() != numel:
+        raise ValueError(f"{what} must be a contiguous {dtype_name} tensor of {numel} elements")
+    return t.data_ptr()
+
+
+def flic_label_batch_host(b: Batch, handles, host_ranges, host_labels, groups: int = 0,
+                          input_ready: bool = False, stream=None) -> None:
+    """Label frames held in host memory, packed back to back (frame i's rows*cols values
+    right after frame i-1's): host_ranges float32, host_labels int32, both page-locked for
+    the copies to overlap the labelling.  The labels are in host_labels once the work on
+    `stream` has finished (e.g. after torch.cuda.synchronize()).  input_ready: the readings
+    are already in host_ranges, so the call need not wait for earlier work on `stream`
+    (consecutive calls overlap)."""
+    n = len(handles)
+    total = sum(h.npix for h in handles)
+    hs = (ctypes.c_void_p * n)(*[h.ptr for h in handles])
+    _check(_lib.flic_label_batch_host(b.ptr, hs, n, _hptr(host_ranges, "float32", total, "host_ranges"),
+                                      _hptr(host_labels, "int32", total, "host_labels"),
+                                      int(groups), FLIC_HOST_INPUT_READY if input_ready else 0,
+                                      _stream(stream)))
 
 
 def flic_device_status(h: Handle, clear: bool = True) -> int:

@@ -503,6 +503,30 @@ def main():
     flic.flic_label_batch(batches[0], bargs[0], stream)  # the device path on the same frames
     torch.cuda.synchronize()
     e2e_ok = bool(np.array_equal(host_out.numpy(), lab_dev[0].cpu().numpy()))
+    # the link's limit for this step: one step's upload and download at once, on two
+    # streams, nothing else running (best of 8)
+    up_s, dn_s = torch.cuda.Stream(), torch.cuda.Stream()
+    link_ms = {"both": [], "h2d": [], "d2h": []}
+    for rep in range(8):
+        for kind in link_ms:
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            c0.record(stream)
+            up_s.wait_event(c0)
+            dn_s.wait_event(c0)
+            if kind != "d2h":
+                with torch.cuda.stream(up_s):
+                    rng_dev[1].copy_(host_in, non_blocking=True)
+            if kind != "h2d":
+                with torch.cuda.stream(dn_s):
+                    host_out.copy_(lab_dev[1], non_blocking=True)
+            stream.wait_stream(up_s)
+            stream.wait_stream(dn_s)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            link_ms[kind].append(c0.elapsed_time(c1))
+    link = {k: round(min(v[2:]), 4) for k, v in link_ms.items()}
     hb.close()
     e2e = {"value": round(total_px * world / (e2e_ms / 1e3) / 1e6, 1), "unit": UNIT,
            "h2d_bytes_per_step": 4 * total_px, "d2h_bytes_per_step": 4 * total_px,
@@ -511,6 +535,11 @@ def main():
                   "run under the previous step's downloads)",
            "ms_per_step_by_groups": {str(k): v for k, v in sorted(e2e_groups.items())},
            "ms_per_step_each_call_ordered_on_stream": e2e_ordered,
+           "copy_floor": {"ms_h2d_and_d2h_at_once": link["both"], "ms_h2d_alone": link["h2d"],
+                          "ms_d2h_alone": link["d2h"],
+                          "frac": round(link["both"] / e2e_ms, 4),
+                          "note": "one step's 4 B/px upload and 4 B/px download as plain "
+                                  "copies on two streams: the link's limit for e2e"},
            "labels_match_device_path": e2e_ok}
     sane &= e2e_ok
 

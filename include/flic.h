@@ -235,7 +235,9 @@ flic_status flic_label_batch_host(flic_batch b, const flic_handle* hs, int32_t n
 
 /*
  * Launch-shape tuning (no counterpart in the paper).  px_per_cta: target pixels per
- * strip, the tile of the shared-memory union pass (0 = built-in default, 16384);
+ * strip, the tile of the shared-memory union pass (0 = built-in default: 2048 for a
+ * handle's single-frame calls, where more blocks per frame lower the latency, and 16384
+ * for a batch object, where many frames fill the GPU);
  * threads: threads per block (128..512, multiple of 32; 0 = 512); max_strips: upper
  * bound on the strips one frame is split into (1..64; 0 = 64); ctas_per_sm (batch only):
  * cap on resident blocks per SM (0 = as many as fit).  flic_set_tuning applies to the

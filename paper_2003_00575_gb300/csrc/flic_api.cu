@@ -44,6 +44,10 @@ struct Tuning {
     int p3_delay = 8;     // batch: P3 tasks this many waves of blocks after their frame
 };
 
+// Strip size of a handle's single-frame calls: one frame alone leaves most SMs idle with
+// batch-sized strips, so smaller strips (more blocks per frame) give the lower latency.
+constexpr int kSingleFramePx = 2048;
+
 // flic_label_batch_host: groups of frames whose copies overlap the labelling of others
 constexpr int kDefaultHostGroups = 4;
 constexpr int kMaxHostGroups = 16;
@@ -149,7 +153,7 @@ struct flic_ctx {
     int iter_limit = 0;
     int32_t* d_counters = nullptr;  // task queue of single-frame launches
     int resident = 1;               // blocks of the label kernel that fit at once
-    Tuning tune;
+    Tuning tune{kSingleFramePx};
     StripPlan plan;
     uint64_t uid = 0;      // unique per handle ever created (pointers can be reused)
     uint64_t version = 0;  // bumped whenever a setting a batch descriptor copies changes
@@ -519,7 +523,7 @@ flic_status flic_set_tuning(flic_handle h, int32_t px_per_cta, int32_t threads, 
         (threads && (threads < 128 || threads > 512 || threads % 32)))
         return fail(FLIC_ERR_INVALID, "bad tuning values");
     Tuning old = h->tune;
-    Tuning def;
+    Tuning def{kSingleFramePx};
     h->tune.px_per_cta = px_per_cta ? px_per_cta : def.px_per_cta;
     h->tune.threads = threads ? threads : def.threads;
     h->tune.max_strips = max_strips ? max_strips : def.max_strips;

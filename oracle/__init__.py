@@ -66,8 +66,12 @@ def _load():
         lib.oracle_pred_paper_form.argtypes = [f32, f32, f32, f32]
         lib.oracle_pred_paper_form.restype = i32
         lib.oracle_edges.argtypes = [i32, i32, P, P, P, i32, f32, i32, P]
+        lib.oracle_edges_ex.argtypes = [i32, i32, P, P, P, i32, f32, i32, i32, P]
+        lib.oracle_edges_ex.restype = None
         lib.oracle_edges.restype = None
         lib.oracle_label.argtypes = [i32, i32, P, P, P, i32, f32, i32, P]
+        lib.oracle_label_ex.argtypes = [i32, i32, P, P, P, i32, f32, i32, i32, P]
+        lib.oracle_label_ex.restype = i64
         lib.oracle_label.restype = i64
         lib.oracle_flips.argtypes = [i32, i32, P, P, f64, P, P, i32, f32, i32, P, P]
         lib.oracle_flips.restype = None
@@ -123,26 +127,30 @@ def pred_paper_form(a: float, b: float, C2: float, delta: float) -> bool:
 
 
 def edges(range_img, elevation, az_step: float, delta: float, skip: int, wrap: bool = True,
-          exact_ray: bool = False):
-    """uint16 [rows, cols] edge bits: bit k-1 horizontal (+k, wrap), bit 8+k-1 vertical (+k)."""
+          exact_ray: bool = False, lattice: bool = False):
+    """uint16 [rows, cols] edge bits: bit k-1 horizontal (+k, wrap), bit 8+k-1 vertical (+k).
+    lattice: the sparse Map Connection (§III-B-2), offset 1 from every pixel and offset S
+    only from pixels whose row and column are multiples of S."""
     rng = _f32(range_img)
     R, C = rng.shape
     kv, kh = tables(elevation, az_step, skip, exact_ray)
     mask = np.zeros((R, C), np.uint16)
-    _load().oracle_edges(R, C, _ptr(rng), _ptr(kv), _ptr(kh), skip, float(np.float32(delta)),
-                         int(bool(wrap)), _ptr(mask))
+    _load().oracle_edges_ex(R, C, _ptr(rng), _ptr(kv), _ptr(kh), skip, float(np.float32(delta)),
+                            int(bool(wrap)), int(bool(lattice)), _ptr(mask))
     return mask
 
 
 def label(range_img, elevation, az_step: float, delta: float, skip: int, wrap: bool = True,
-          exact_ray: bool = False):
-    """int32 [rows, cols] labels: min linear index of the component, -1 for invalid."""
+          exact_ray: bool = False, lattice: bool = False):
+    """int32 [rows, cols] labels: min linear index of the component, -1 for invalid.
+    lattice: the sparse Map Connection of §III-B-2 (see edges)."""
     rng = _f32(range_img)
     R, C = rng.shape
     kv, kh = tables(elevation, az_step, skip, exact_ray)
     out = np.empty((R, C), np.int32)
-    n = _load().oracle_label(R, C, _ptr(rng), _ptr(kv), _ptr(kh), skip,
-                             float(np.float32(delta)), int(bool(wrap)), _ptr(out))
+    n = _load().oracle_label_ex(R, C, _ptr(rng), _ptr(kv), _ptr(kh), skip,
+                                float(np.float32(delta)), int(bool(wrap)), int(bool(lattice)),
+                                _ptr(out))
     if n < 0:
         raise MemoryError("oracle_label: out of memory")
     return out

@@ -21,6 +21,9 @@
  *   oracle_scatter    labels back onto the points (§I, Fig. 1)
  *   oracle_ground     ground extraction by the angle to the reading above (§III-A, Eq. 1
  *                     in its tangent form), with the optional height-line exception
+ *   oracle_edges_ex,  the same with the paper's sparse Map Connection (§III-B-2): besides
+ *   oracle_label_ex   the direct neighbours, only every S-th point in each direction is
+ *                     joined, to the S-th point further on (a sub-lattice map)
  */
 #include <float.h>
 #include <math.h>
@@ -107,8 +110,29 @@ static float oracle_delta2(float delta) { return delta * delta; }
  * bit k-1 = edge to (r, (c+k) mod C) (no wrap: only when c+k < C),
  * bit 8+k-1 = edge to (r+k, c) when r+k < R.
  */
+/*
+ * Which offsets a pixel's pairs may use.  Offsets 1..S from every pixel is the general
+ * reading of §III-B-2.  With lattice != 0 it is the paper's sparse map instead: the
+ * direct neighbours (offset 1) of every pixel, and offset S only from the points of the
+ * sub-lattice of every S-th row and every S-th column ("connecting only every n-th
+ * point", with n = S); (r, c) is the pair's left or upper end, c its column before any
+ * wrap.
+ */
+static int oracle_offset_used(int32_t lattice, int32_t S, int32_t k, int32_t r, int32_t c) {
+    if (!lattice || k == 1) return 1;
+    return k == S && r % S == 0 && c % S == 0;
+}
+
+void oracle_edges_ex(int32_t R, int32_t C, const float* range, const float* Kv, const float* Kh,
+                     int32_t S, float delta, int32_t wrap, int32_t lattice, uint16_t* mask);
+
 void oracle_edges(int32_t R, int32_t C, const float* range, const float* Kv, const float* Kh,
                   int32_t S, float delta, int32_t wrap, uint16_t* mask) {
+    oracle_edges_ex(R, C, range, Kv, Kh, S, delta, wrap, 0, mask);
+}
+
+void oracle_edges_ex(int32_t R, int32_t C, const float* range, const float* Kv, const float* Kh,
+                     int32_t S, float delta, int32_t wrap, int32_t lattice, uint16_t* mask) {
     float delta2 = oracle_delta2(delta);
     for (int32_t r = 0; r < R; ++r) {
         for (int32_t c = 0; c < C; ++c) {
@@ -116,6 +140,7 @@ void oracle_edges(int32_t R, int32_t C, const float* range, const float* Kv, con
             float a = range[(int64_t)r * C + c];
             if (oracle_valid(a)) {
                 for (int32_t k = 1; k <= S; ++k) {
+                    if (!oracle_offset_used(lattice, S, k, r, c)) continue;
                     int32_t cc = c + k;
                     int has = 1;
                     if (cc >= C) {
@@ -148,8 +173,20 @@ void oracle_edges(int32_t R, int32_t C, const float* range, const float* Kv, con
  * (smaller) row, each with the offset k that reaches it.
  * Returns the number of components, or -1 if memory for the queue is unavailable.
  */
+int64_t oracle_label_ex(int32_t R, int32_t C, const float* range, const float* Kv,
+                        const float* Kh, int32_t S, float delta, int32_t wrap, int32_t lattice,
+                        int32_t* labels);
+
 int64_t oracle_label(int32_t R, int32_t C, const float* range, const float* Kv, const float* Kh,
                      int32_t S, float delta, int32_t wrap, int32_t* labels) {
+    return oracle_label_ex(R, C, range, Kv, Kh, S, delta, wrap, 0, labels);
+}
+
+/* oracle_label with the pairs restricted by oracle_offset_used (lattice != 0: the sparse
+ * Map Connection of §III-B-2). */
+int64_t oracle_label_ex(int32_t R, int32_t C, const float* range, const float* Kv,
+                        const float* Kh, int32_t S, float delta, int32_t wrap, int32_t lattice,
+                        int32_t* labels) {
     int64_t N = (int64_t)R * C;
     float delta2 = oracle_delta2(delta);
     int32_t* queue = (int32_t*)malloc((size_t)(N > 0 ? N : 1) * sizeof(int32_t));
@@ -174,6 +211,8 @@ int64_t oracle_label(int32_t R, int32_t C, const float* range, const float* Kv, 
                         if (!wrap) continue;
                         vc = ((vc % C) + C) % C;
                     }
+                    /* the left end: u itself, or v when v lies k columns to the left */
+                    if (!oracle_offset_used(lattice, S, k, ur, dir > 0 ? uc : vc)) continue;
                     int32_t v = ur * C + vc;
                     if (labels[v] != -1) continue;
                     float b = range[v];
@@ -189,6 +228,7 @@ int64_t oracle_label(int32_t R, int32_t C, const float* range, const float* Kv, 
                     int32_t v = vr * C + uc;
                     if (labels[v] != -1) continue;
                     int32_t top = dir > 0 ? ur : vr;
+                    if (!oracle_offset_used(lattice, S, k, top, uc)) continue;
                     float b = range[v];
                     if (oracle_valid(b) && oracle_pred(a, b, Kv[top * S + k - 1], delta2)) {
                         labels[v] = (int32_t)p0;

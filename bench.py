@@ -443,6 +443,17 @@ def main():
                 torch.cuda.synchronize()
                 seg[f"{cname}_S{S}_{mode}"] = quality.scores(lab_q.cpu().numpy(), gt)
                 hq.close()
+        # the paper's one Map Connection (every second point, §III-B-2) against offsets 1..2
+        rng_q = np.where(gt == 0, np.float32(0), fr.range).astype(np.float32)
+        for key, lat in (("S2", False), ("1MC_every_2nd_point", True)):
+            hq = flic.flic_create(R, C, fr.sensor.elevation, fr.sensor.az_step, fr.delta, 2,
+                                  lattice=lat)
+            lab_q = torch.empty(R * C, dtype=torch.int32, device=dev)
+            flic.flic_label(hq, torch.from_numpy(np.ascontiguousarray(rng_q).reshape(-1)).to(dev),
+                            lab_q, stream)
+            torch.cuda.synchronize()
+            seg[f"{cname}_{key}_gt_ground_removed"] = quality.scores(lab_q.cpu().numpy(), gt)
+            hq.close()
     seg["note"] = ("§IV metrics against the ray caster's object ids (instances >= 100 px); "
                    "the paper's own numbers are on SemanticKITTI, not comparable")
 

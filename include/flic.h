@@ -41,6 +41,8 @@
  *                 alpha = |elev[r+k] - elev[r]|       (K table Kv[r][k-1])
  *   Horizontal pair (r,c)-(r,(c+k) mod cols), k = 1..S (no wrap: c+k < cols):
  *                 alpha = k * az_step                 (K table Kh[r][k-1])
+ *   With FLIC_FLAG_SUBLATTICE a pair of offset k >= 2 exists only for k = S and (r,c) with
+ *   r and c multiples of S.
  * Labels: label[p] = the minimum linear index over p's connected component when p is
  * valid, -1 otherwise.
  */
@@ -74,6 +76,11 @@ typedef enum {
  * cos(alpha) = cos^2(e) cos(k az_step) + sin^2(e), i.e. K = 4 cos^2(e) sin^2(k az_step / 2),
  * instead of the paper's k * az_step (§III-B) */
 #define FLIC_FLAG_EXACT_RAY 0x2u
+/* the paper's sparse Map Connection (§III-B-2, "connecting only every n-th point", n = skip):
+ * offset 1 from every pixel, offset skip only from pixels whose row and column are both
+ * multiples of skip (the pair's left or upper end; its column before any wrap), offsets
+ * 2..skip-1 not at all.  Without it every pixel uses every offset 1..skip. */
+#define FLIC_FLAG_SUBLATTICE 0x4u
 
 /* Largest frame the labeller accepts: rows * cols <= FLIC_MAX_PIXELS, rows <= FLIC_MAX_ROWS.
  * A frame is split into at most 64 full-height column strips of at most 32768 (padded)

@@ -229,6 +229,7 @@ flic::FrameDesc frame_desc(const flic_ctx* h, const float* range, int32_t* label
     f.strip_w = pl.strip_w;
     f.pitch_log2 = pl.pitch_log2;
     f.iter_limit = h->iter_limit;
+    f.lattice = (h->flags & FLIC_FLAG_SUBLATTICE) ? 1 : 0;
     f.gnd = h->d_gnd;
     f.gnd_tan = h->gnd_tan;
     f.gnd_height = h->gnd_height;
@@ -358,7 +359,7 @@ flic_status flic_create_ex(int32_t rows, int32_t cols, const double* elevation, 
     if (!(delta > 0.0f) || !std::isfinite(delta))
         return fail(FLIC_ERR_INVALID, "delta must be positive and finite");
     if (skip < 1 || skip > FLIC_MAX_SKIP) return fail(FLIC_ERR_INVALID, "skip must be 1..%d", FLIC_MAX_SKIP);
-    if (flags & ~(FLIC_FLAG_NO_WRAP | FLIC_FLAG_EXACT_RAY))
+    if (flags & ~(FLIC_FLAG_NO_WRAP | FLIC_FLAG_EXACT_RAY | FLIC_FLAG_SUBLATTICE))
         return fail(FLIC_ERR_INVALID, "unknown flags 0x%x", flags);
 
     flic_ctx* h = new flic_ctx();

@@ -29,7 +29,8 @@ struct FrameDesc {
     int32_t strip_w;      // columns per strip (last strip may be narrower)
     int32_t pitch_log2;   // local row pitch of the shared-memory forest = 1 << pitch_log2
     int32_t iter_limit;   // bound of every device loop; 0 -> kDefaultIterLimit
-    int32_t pad_;
+    int32_t lattice;      // 1: offsets 2..skip-1 unused, offset skip only from pixels whose
+                          // row and column are multiples of skip (sparse Map Connection)
     // ground extraction (flic_set_ground), nullptr: off.  Row r: [0] sin, [1] cos of the
     // angle to row r-1, [2] tan(gamma - theta), [3] tan(gamma + theta) (gamma = -elevation
     // of row r-1, +-inf past +-90 degrees), [4] sin, [5] cos of row r's elevation.

@@ -67,6 +67,7 @@ struct Strip {
     int R, C, S;
     float delta2;
     bool wrap;
+    bool lattice;  // sparse Map Connection (FrameDesc::lattice)
     int c0, W;     // first column and width of the strip
     int sh;        // local pitch = 1 << sh (>= 32, >= W)
     int RP;        // row pitch of the staged readings (>= W + S, multiple of 4)
@@ -280,6 +281,34 @@ __device__ __forceinline__ void mask_chunk(const Strip& s, const float* row, int
         edge_d2_pair(a, b, d, kh[k - 1], kv[k - 1], dh, dv);
         w[k] = __ballot_sync(kFull, va & (b > 0.0f) & (dh <= s.delta2));
         w[S + k] = __ballot_sync(kFull, va & (d > 0.0f) & (dv <= s.delta2));
+    }
+}
+
+// 1b. The sparse Map Connection (§III-B-2, every S-th point joined at offset S), applied to
+//     the ballot words of the whole strip (one thread per row segment): offsets 2..S-1
+//     dropped, offset S kept only where the row and the global column are multiples of S.
+template <int S>
+__device__ void lattice_words(const Strip& s, const Carve& sm) {
+    if constexpr (S >= 2) {
+        constexpr int NP = Words<S>::NP;
+        unsigned pat = 0;  // bits 0, S, 2S, ... of a word
+#pragma unroll
+        for (int b = 0; b < 32; b += S) pat |= 1u << b;
+        const int nsl = s.sh - 5;
+        const int n = s.R << nsl;
+        for (int u = threadIdx.x; u < n; u += blockDim.x) {
+            unsigned* w = sm.words + (size_t)u * NP;
+            const int r = u >> nsl;
+            const int base = s.c0 + ((u & ((1 << nsl) - 1)) << 5);  // global column of bit 0
+            const unsigned keep = r % S == 0 ? pat << ((S - base % S) % S) : 0u;
+#pragma unroll
+            for (int k = 2; k < S; ++k) {
+                w[k] = 0u;
+                w[S + k] = 0u;
+            }
+            w[S] &= keep;
+            w[2 * S] &= keep;
+        }
     }
 }
 
@@ -517,6 +546,10 @@ template <int S>
 __device__ void phase1_strip(const Strip& s, const Carve& sm) {
     mask_rows<S>(s, sm);
     __syncthreads();  // the staged readings are dead from here on
+    if (s.lattice) {
+        lattice_words<S>(s, sm);
+        __syncthreads();
+    }
     init_runs<S>(s, sm);
     __syncthreads();
     link_runs<S>(s, sm);
@@ -583,7 +616,10 @@ __device__ void border_merge_s(const FrameDesc& f, int b, int limit,
         const int ga = ok ? __ldcg(f.labels + row + first + j) : 0;
         const int gb = ok ? __ldcg(f.labels + row + tc) : 0;
         const float K = __ldg(f.kh + (ok ? r : 0) * S + k - 1);
-        const bool e = av > 0.0f && dv > 0.0f && edge_pred(av, dv, K, f.delta2);
+        // the sparse Map Connection: offset S from lattice points, offset 1 from all
+        const bool used = !f.lattice || k == 1 ||
+                          (k == S && r % S == 0 && (first + j) % S == 0);
+        const bool e = used && av > 0.0f && dv > 0.0f && edge_pred(av, dv, K, f.delta2);
         const int pa = __shfl_up_sync(kFull, ga, 1);
         const int pb = __shfl_up_sync(kFull, gb, 1);
         const unsigned em = __ballot_sync(kFull, e);
@@ -612,6 +648,7 @@ __device__ void border_merge_narrow(const FrameDesc& f, int limit) {
         const float a = load_range_g(f, r, c);
         if (!(a > 0.0f)) continue;
         for (int k = C - c; k <= S; ++k) {
+            if (f.lattice && k != 1 && (k != S || r % S != 0 || c % S != 0)) continue;
             const int tc = (c + k) % C;
             const float d = load_range_g(f, r, tc);
             if (d > 0.0f && edge_pred(a, d, __ldg(f.kh + r * S + k - 1), f.delta2)) {
@@ -806,6 +843,7 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
             s.gnd = f.rows >= 2 ? f.gnd : nullptr;
             s.gnd_tan = f.gnd_tan;
             s.gnd_height = f.gnd_height;
+            s.lattice = f.lattice != 0;
             const Carve sm = carve(smem_raw, s);
             phase1_stage(s, sm, &tma_bar, parity);
             if (s.bulk) parity ^= 1u;
@@ -881,6 +919,9 @@ __global__ void flic_edges_kernel(const FrameDesc f, uint16_t* __restrict__ mask
         unsigned m = 0;
         if (a > 0.0f) {
             for (int k = 1; k <= f.skip; ++k) {
+                if (f.lattice && k != 1 &&
+                    (k != f.skip || r % f.skip != 0 || c % f.skip != 0))
+                    continue;  // the sparse Map Connection
                 int cc = c + k;
                 bool has = true;
                 if (cc >= f.cols) {

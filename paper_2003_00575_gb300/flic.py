@@ -25,6 +25,7 @@ FLIC_ERR_BUSY = 5
 FLIC_ERR_UNSUPPORTED = 6
 FLIC_FLAG_NO_WRAP = 1
 FLIC_FLAG_EXACT_RAY = 2
+FLIC_FLAG_SUBLATTICE = 4
 FLIC_HOST_INPUT_READY = 1
 FLIC_MAX_PIXELS = 1 << 21
 FLIC_MAX_ROWS = 512
@@ -158,12 +159,15 @@ def flic_abi_version() -> int:
 
 
 def flic_create(rows: int, cols: int, elevation, az_step: float, delta: float, skip: int,
-                wrap: bool = True, exact_ray: bool = False) -> Handle:
+                wrap: bool = True, exact_ray: bool = False, lattice: bool = False) -> Handle:
+    """lattice: the paper's sparse Map Connection (every skip-th point joined at offset
+    skip, direct neighbours everywhere) instead of offsets 1..skip from every pixel."""
     elev = np.ascontiguousarray(elevation, dtype=np.float64)
     if elev.shape != (rows,):
         raise ValueError("elevation must have one entry per row")
     out = ctypes.c_void_p()
-    flags = (0 if wrap else FLIC_FLAG_NO_WRAP) | (FLIC_FLAG_EXACT_RAY if exact_ray else 0)
+    flags = ((0 if wrap else FLIC_FLAG_NO_WRAP) | (FLIC_FLAG_EXACT_RAY if exact_ray else 0)
+             | (FLIC_FLAG_SUBLATTICE if lattice else 0))
     _check(_lib.flic_create_ex(rows, cols, elev.ctypes.data, float(az_step), float(delta), skip,
                                flags, ctypes.byref(out)))
     return Handle(out.value, rows, cols, skip, float(np.float32(delta)), wrap)

@@ -130,16 +130,21 @@ def source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def committed_traffic():
-    """DRAM bytes per launch from the committed ncu summary, if taken on these sources."""
+def committed_counter(name: str):
+    """A per-launch counter from the committed ncu summary, if taken on these sources."""
     if not os.path.exists(PROFILE_NOTE):
         return None
     text = open(PROFILE_NOTE).read()
     sha = re.search(r"source_sha256_16:\s*([0-9a-f]+)", text)
-    tr = re.search(r"traffic_bytes_per_launch_full_batch:\s*([0-9.eE+]+)", text)
-    if not sha or not tr or sha.group(1) != source_sha():
+    val = re.search(name + r":\s*([0-9.eE+]+)", text)
+    if not sha or not val or sha.group(1) != source_sha():
         return None
-    return float(tr.group(1))
+    return float(val.group(1))
+
+
+def committed_traffic():
+    """DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum)."""
+    return committed_counter("traffic_bytes_per_launch_full_batch")
 
 
 def load_peak():
@@ -372,6 +377,20 @@ def main():
                        "frac": round(alu_achieved / alu_peak, 4) if alu_peak else None,
                        "ops_per_launch": ops,
                        "peak_source": f"derived: {nsm} SMs x 128 fp32 lanes x max SM clock"}
+    # the roof that binds this kernel: instruction issue, one warp instruction per cycle per
+    # scheduler (4 per SM) at the sampled maximum SM clock, against the warp instructions
+    # ncu counted for one launch of the same sources (null once the sources have changed)
+    inst = committed_counter("warp_instructions_per_launch_full_batch")
+    issue_peak = nsm * 4 * clocks["sm_max_mhz"] * 1e6 / 1e9 if clocks["sm_max_mhz"] else None
+    issue_achieved = inst / mean_launch_s / 1e9 if inst else None
+    roofline["issue"] = {"bound": "issue",
+                         "achieved": round(issue_achieved, 1) if issue_achieved else None,
+                         "peak": round(issue_peak, 1) if issue_peak else None,
+                         "unit": "G warp-instructions/s",
+                         "frac": round(issue_achieved / issue_peak, 4)
+                         if issue_achieved and issue_peak else None,
+                         "warp_instructions_per_launch": inst,
+                         "peak_source": f"derived: {nsm} SMs x 4 schedulers x max SM clock"}
 
     # ---- cluster candidates (§III-B, the paper's minimum of 100 points) over the batch's
     # fresh labels: flic_filter_relabel_batch alone is timed
@@ -454,6 +473,18 @@ def main():
             torch.cuda.synchronize()
             seg[f"{cname}_{key}_gt_ground_removed"] = quality.scores(lab_q.cpu().numpy(), gt)
             hq.close()
+        # the distance-threshold study (§IV, parameter study of delta): IoU_mu over delta
+        rng_t = torch.from_numpy(np.ascontiguousarray(rng_q).reshape(-1)).to(dev)
+        for S in sorted({1, fr.skip}):
+            sweep = {}
+            for dl in (0.1, 0.2, 0.3, 0.4, 0.5, 0.6, 0.8, 1.0, 1.5, 2.0):
+                hq = flic.flic_create(R, C, fr.sensor.elevation, fr.sensor.az_step, dl, S)
+                lab_q = torch.empty(R * C, dtype=torch.int32, device=dev)
+                flic.flic_label(hq, rng_t, lab_q, stream)
+                torch.cuda.synchronize()
+                sweep[str(dl)] = quality.scores(lab_q.cpu().numpy(), gt).get("iou_mu")
+                hq.close()
+            seg[f"{cname}_S{S}_iou_mu_by_delta_m"] = sweep
     seg["note"] = ("§IV metrics against the ray caster's object ids (instances >= 100 px); "
                    "the paper's own numbers are on SemanticKITTI, not comparable")
 
@@ -523,6 +554,9 @@ def main():
             c0 = torch.cuda.Event(enable_timing=True)
             c1 = torch.cuda.Event(enable_timing=True)
             torch.cuda.synchronize()
+            # a short sleep on the stream first, so that the copies are queued by the time
+            # the start event is reached (the host's enqueue time is not the link's)
+            torch.cuda._sleep(200_000)
             c0.record(stream)
             up_s.wait_event(c0)
             dn_s.wait_event(c0)

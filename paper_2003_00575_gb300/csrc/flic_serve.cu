@@ -65,6 +65,9 @@ struct Flight {  // one batch in flight on one lane
 struct Lane {
     cudaStream_t stream = nullptr;
     flic_batch batch = nullptr;
+    // small batches (too few batch-sized strips to give every SM one): 2048-pixel strips,
+    // so that more blocks share the frames and the batch finishes sooner
+    flic_batch batch_small = nullptr;
     bool busy = false;
     Flight f;
 };
@@ -89,6 +92,7 @@ struct flic_server_ctx {
     std::vector<Slot> slots;
     std::deque<Lane> lanes;  // not movable (atomics): built in place
     int max_batch = 0;
+    size_t small_px = 0;  // batches of fewer pixels use the lane's small-strip object
     int max_queue = 0;
     int64_t slot_bytes = 0;
     std::mutex mu;
@@ -116,6 +120,7 @@ void free_server(flic_server_ctx* s) {
     }
     for (Lane& ln : s->lanes) {
         if (ln.batch) flic_batch_destroy(ln.batch);
+        if (ln.batch_small) flic_batch_destroy(ln.batch_small);
         if (ln.stream) cudaStreamDestroy(ln.stream);
     }
     delete s;
@@ -204,10 +209,18 @@ extern "C" flic_status flic_server_create(const flic_handle* sensors, int32_t ns
     for (Lane& ln : s->lanes) {
         cudaError_t e = cudaStreamCreateWithFlags(&ln.stream, cudaStreamNonBlocking);
         flic_status st = e == cudaSuccess ? flic_batch_create(max_batch, &ln.batch) : FLIC_ERR_CUDA;
+        if (st == FLIC_OK) st = flic_batch_create(max_batch, &ln.batch_small);
+        if (st == FLIC_OK) st = flic_batch_set_tuning(ln.batch_small, 2048, 0, 0, 0);
         if (st != FLIC_OK) {
             free_server(s);
             return srv_fail(st, "flic_server_create: stream or batch object failed");
         }
+    }
+    {
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        s->small_px = (size_t)std::max(nsm, 1) * 16384;  // one batch-sized strip per SM
     }
     s->dispatcher = std::thread(dispatch_loop, s);
     *out = s;
@@ -252,7 +265,13 @@ void launch(flic_server_ctx* s, Lane& ln, std::vector<Request>& take, std::vecto
         rs[i] = sl.d_range;
         ls[i] = sl.d_labels;
     }
-    note(flic_label_batch(ln.batch, hs.data(), rs.data(), ls.data(), n, st));
+    size_t px = 0;
+    for (int i = 0; i < n; ++i) {
+        const Sensor& sn = s->sensors[f.reqs[i].sensor];
+        px += (size_t)sn.rows * sn.cols;
+    }
+    note(flic_label_batch(px < s->small_px ? ln.batch_small : ln.batch, hs.data(), rs.data(),
+                          ls.data(), n, st));
     for (int i = 0; i < n; ++i) {
         const Request& q = f.reqs[i];
         const Slot& sl = s->slots[f.slots[i]];

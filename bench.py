@@ -77,6 +77,9 @@ def parse_args():
     p.add_argument("--tuning", type=str, default="",
                    help="px_per_cta,threads,max_strips,ctas_per_sm for the batch (skips autotuning)")
     p.add_argument("--no-autotune", action="store_true")
+    p.add_argument("--proj-scale", type=int, default=1,
+                   help="repeat the c3 cloud this many times in the projection section "
+                        "(a cloud larger than L2 for DRAM counters)")
     p.add_argument("--serve-seconds", type=float, default=3.0,
                    help="short serving sweep (0 = skip); the full sweep is serve.py")
     return p.parse_args()
@@ -592,9 +595,10 @@ def main():
     f3 = synth.config_c3()
     s3 = f3.sensor
     h3 = flic.flic_create(s3.rows, s3.cols, s3.elevation, s3.az_step, f3.delta, f3.skip)
-    xyz = torch.from_numpy(f3.xyz).to(dev)
+    cloud = np.tile(f3.xyz, (max(1, args.proj_scale), 1))  # copies tie; the lowest index wins
+    xyz = torch.from_numpy(cloud).to(dev)
     rimg = torch.empty(s3.rows * s3.cols, dtype=torch.float32, device=dev)
-    pix = torch.empty(f3.xyz.shape[0], dtype=torch.int32, device=dev)
+    pix = torch.empty(cloud.shape[0], dtype=torch.int32, device=dev)
     lab3 = torch.empty(s3.rows * s3.cols, dtype=torch.int32, device=dev)
     plab = torch.empty_like(pix)
     pe = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
@@ -613,13 +617,14 @@ def main():
                              pe[2].elapsed_time(pe[3]), pe[0].elapsed_time(pe[3])])
     lp = np.array(lat_proj)
     projection = {
-        "workload": "c3 128x2048 S5 delta 0.4, 262,144 xyz points",
+        "workload": f"c3 128x2048 S5 delta 0.4, {cloud.shape[0]:,} xyz points"
+                    + (f" (the c3 cloud {args.proj_scale} times)" if args.proj_scale > 1 else ""),
         "ms_project": round(float(np.median(lp[:, 0])), 4),
         "ms_label": round(float(np.median(lp[:, 1])), 4),
         "ms_scatter": round(float(np.median(lp[:, 2])), 4),
         "latency_ms_p50": round(pct(lp[:, 3], 50), 4),
         "latency_ms_p99": round(pct(lp[:, 3], 99), 4),
-        "mpoints_per_s": round(f3.xyz.shape[0] / (float(np.median(lp[:, 3])) / 1e3) / 1e6, 1),
+        "mpoints_per_s": round(cloud.shape[0] / (float(np.median(lp[:, 3])) / 1e3) / 1e6, 1),
     }
     h3.close()
 

@@ -510,24 +510,33 @@ __device__ void write_labels(const Strip& s, const Carve& sm) {
     const bool vec = ((s.C & 3) == 0) && ((s.c0 & 3) == 0) &&
                      ((reinterpret_cast<uintptr_t>(s.labels) & 15) == 0);
     int last_s = -1, last_root = -1;
+    // the global label of the run starting at local pixel st (lanes meet few runs)
+    auto root_of = [&](int st) {
+        if (st != last_s) {
+            last_root = global_of(s, vp[slot(st)]);
+            last_s = st;
+        }
+        return last_root;
+    };
     for (int r = warp; r < s.R; r += nwarps) {
         int32_t* out = s.labels + (size_t)r * s.C + s.c0;
         for (int c = lane * 4; c < s.W; c += 128) {
             const int u = (r << nsl) + (c >> 5);
-            const unsigned va = wd(0, u);
-            const unsigned rs = wd.starts(u);
-            int v[4];
+            const int sh = c & 31;  // c is a multiple of 4: the four pixels share a segment
+            const unsigned v4 = (wd(0, u) >> sh) & 0xFu;  // no bit is set at or past column W
+            int v[4] = {-1, -1, -1, -1};
+            if (v4) {
+                const unsigned rs = wd.starts(u);
+                const unsigned r4 = (rs >> sh) & 0xFu;
+                const int base = (u << 5) + sh;
+                // a valid pixel that starts no run continues the run of the pixel before it,
+                // so one run start is searched for (the first pixel's), the rest are bits
+                int root = (v4 & 1u) ? root_of((u << 5) + top_bit(rs & upto(sh))) : -1;
+                v[0] = root;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const int cc = (c & 31) + q;  // c is a multiple of 4: same segment
-                v[q] = -1;
-                if ((va >> cc) & 1u) {  // no bit is set at or past column W
-                    const int st = (u << 5) + top_bit(rs & upto(cc));
-                    if (st != last_s) {
-                        last_root = global_of(s, vp[slot(st)]);
-                        last_s = st;
-                    }
-                    v[q] = last_root;
+                for (int q = 1; q < 4; ++q) {
+                    if ((r4 >> q) & 1u) root = root_of(base + q);
+                    v[q] = ((v4 >> q) & 1u) ? root : -1;
                 }
             }
             if (vec && c + 4 <= s.W) {

@@ -359,9 +359,10 @@ flic_status flic_debug_set_iter_limit(flic_handle h, int32_t limit);
  *                   range image, labels, xyz, pixel map, point labels); at least one slot
  *                   per sensor is created
  *   max_queue       requests that may wait for a slot before submit refuses (>= 1)
- *   Starts one dispatcher thread.  Each stream has two batch objects: batches too small
- *   to give every SM one 16384-pixel strip are labelled with 2048-pixel strips (lower
- *   latency), larger ones with the batch default.  Errors: INVALID, OOM, CUDA.
+ *   Starts one dispatcher thread.  Each stream has two batch objects: a batch too small
+ *   to give every SM one 16384-pixel strip, launched while no other stream has a batch in
+ *   flight, is labelled with 2048-pixel strips (lower latency); under load, and for
+ *   larger batches, the batch default is used.  Errors: INVALID, OOM, CUDA.
  * flic_server_submit — queue one frame; returns at once:
  *   sensor, kind    sensor index; kind 0 = range image (host_in: rows*cols fp32),
  *                   kind 1 = point cloud (host_in: n*3 fp32 xyz, n <= max_points)

@@ -279,8 +279,9 @@ __device__ __forceinline__ void mask_chunk(const Strip& s, const float* row, int
         const float d = vin ? row[c + k * s.RP] : 0.0f;
         float dh, dv;
         edge_d2_pair(a, b, d, kh[k - 1], kv[k - 1], dh, dv);
-        w[k] = __ballot_sync(kFull, va & (b > 0.0f) & (dh <= s.delta2));
-        w[S + k] = __ballot_sync(kFull, va & (d > 0.0f) & (dv <= s.delta2));
+        // the pixel's own validity is applied once per word
+        w[k] = __ballot_sync(kFull, (b > 0.0f) & (dh <= s.delta2)) & w[0];
+        w[S + k] = __ballot_sync(kFull, (d > 0.0f) & (dv <= s.delta2)) & w[0];
     }
 }
 

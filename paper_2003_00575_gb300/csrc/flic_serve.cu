@@ -270,8 +270,13 @@ void launch(flic_server_ctx* s, Lane& ln, std::vector<Request>& take, std::vecto
         const Sensor& sn = s->sensors[f.reqs[i].sensor];
         px += (size_t)sn.rows * sn.cols;
     }
-    note(flic_label_batch(px < s->small_px ? ln.batch_small : ln.batch, hs.data(), rs.data(),
-                          ls.data(), n, st));
+    // small strips only for a small batch on an otherwise idle GPU: under load the lanes'
+    // batches share the SMs, and batch-sized strips do the work with less overhead
+    bool alone = true;
+    for (const Lane& o : s->lanes)
+        if (&o != &ln && o.busy) alone = false;
+    note(flic_label_batch(alone && px < s->small_px ? ln.batch_small : ln.batch, hs.data(),
+                          rs.data(), ls.data(), n, st));
     for (int i = 0; i < n; ++i) {
         const Request& q = f.reqs[i];
         const Slot& sl = s->slots[f.slots[i]];

@@ -266,7 +266,7 @@ def flic_batch_set_tuning(b: Batch, px_per_cta: int = 0, threads: int = 0, max_s
     _check(_lib.flic_batch_set_tuning(b.ptr, px_per_cta, threads, max_strips, ctas_per_sm))
 
 
-def flic_batch_set_schedule(b: Batch, p3_delay_waves: int = 2) -> None:
+def flic_batch_set_schedule(b: Batch, p3_delay_waves: int = 8) -> None:
     _check(_lib.flic_batch_set_schedule(b.ptr, p3_delay_waves))
 
 

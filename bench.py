@@ -194,6 +194,13 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
             out, _ = self.proc.communicate()
+        return self.parse(out)
+
+    @classmethod
+    def parse(cls, out: str) -> dict:
+        """The clock record of nvidia-smi's CSV lines: median SM clock of the samples under
+        load (utilisation >= 30 %, else all), the highest max clock, the throttle reasons
+        seen active under load."""
         rows = []
         for line in out.strip().splitlines():
             parts = [x.strip() for x in line.split(",")]
@@ -201,7 +208,7 @@ class ClockSampler:
                 continue
             try:
                 rows.append((float(parts[1]), float(parts[2]), float(parts[4]),
-                             [n for n, v in zip(self.NAMES, parts[5:9]) if v == "Active"]))
+                             [n for n, v in zip(cls.NAMES, parts[5:9]) if v == "Active"]))
             except ValueError:
                 continue
         if not rows:

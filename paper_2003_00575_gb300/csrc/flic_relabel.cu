@@ -27,6 +27,13 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kThreads = 256;
+
+// The six kernels are launched with programmatic stream serialization: each one waits
+// here until the grid before it on the stream has completed and its writes are visible,
+// so only the launch of the next grid overlaps the end of the previous one.
+__device__ __forceinline__ void wait_prior_grid() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 constexpr int kWords = kRelabelTile / 32;  // bitmask words per tile (128)
 static_assert(kRelabelTile == 16 * kThreads, "16 pixels per thread");
 
@@ -63,6 +70,7 @@ __device__ __forceinline__ void load4(const RelabelFrame& F, int p, bool vec, in
 }
 
 __global__ void __launch_bounds__(kThreads) relabel_zero(const RelabelLaunch L) {
+    wait_prior_grid();
     const int t = blockIdx.x;
     const RelabelFrame F = frame_at(L, frame_of_tile(L, t));
     const int p0 = (t - F.tile0) * kRelabelTile;
@@ -85,6 +93,7 @@ __global__ void __launch_bounds__(kThreads) relabel_zero(const RelabelLaunch L) 
 constexpr int kHistSlots = 1024;
 
 __global__ void __launch_bounds__(kThreads) relabel_hist(const RelabelLaunch L) {
+    wait_prior_grid();
     __shared__ int keys[kHistSlots];
     __shared__ int vals[kHistSlots];
     const int t = blockIdx.x;
@@ -142,6 +151,7 @@ __global__ void __launch_bounds__(kThreads) relabel_hist(const RelabelLaunch L) 
 
 // Threads 0..127 take one bitmask word each.
 __global__ void __launch_bounds__(kThreads) relabel_count(const RelabelLaunch L) {
+    wait_prior_grid();
     __shared__ int red[kThreads / 32];
     const int t = blockIdx.x;
     const RelabelFrame F = frame_at(L, frame_of_tile(L, t));
@@ -172,6 +182,7 @@ __global__ void __launch_bounds__(kThreads) relabel_count(const RelabelLaunch L)
 // One block per frame: exclusive offsets of its tiles' counts (at most 2^21 / kRelabelTile
 // = 512 tiles, two per thread), and the frame's total.
 __global__ void __launch_bounds__(kThreads) relabel_scan(const RelabelLaunch L) {
+    wait_prior_grid();
     __shared__ int part[kThreads];
     const RelabelFrame F = frame_at(L, blockIdx.x);
     const int nt = (F.npix + kRelabelTile - 1) / kRelabelTile;
@@ -196,6 +207,7 @@ __global__ void __launch_bounds__(kThreads) relabel_scan(const RelabelLaunch L) 
 // Threads 0..127 take one word each: an exclusive prefix of the kept counts over the words
 // (raster order), then every root of the word gets its rank, or -1.
 __global__ void __launch_bounds__(kThreads) relabel_assign(const RelabelLaunch L) {
+    wait_prior_grid();
     __shared__ int red[kThreads / 32];
     __shared__ int warp_off[kThreads / 32];
     const int t = blockIdx.x;
@@ -234,6 +246,7 @@ __global__ void __launch_bounds__(kThreads) relabel_assign(const RelabelLaunch L
 }
 
 __global__ void __launch_bounds__(kThreads) relabel_apply(const RelabelLaunch L) {
+    wait_prior_grid();
     const int t = blockIdx.x;
     const RelabelFrame F = frame_at(L, frame_of_tile(L, t));
     const int p0 = (t - F.tile0) * kRelabelTile;
@@ -263,15 +276,34 @@ __global__ void __launch_bounds__(kThreads) relabel_apply(const RelabelLaunch L)
 
 }  // namespace
 
+namespace {
+
+cudaError_t launch_dependent(void (*kernel)(const RelabelLaunch), int grid,
+                             const RelabelLaunch& L, cudaStream_t stream) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = stream;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, L);
+}
+
+}  // namespace
+
 cudaError_t launch_relabel(const RelabelLaunch& L, cudaStream_t stream) {
     if (L.ntiles <= 0) return cudaSuccess;
-    relabel_zero<<<L.ntiles, kThreads, 0, stream>>>(L);
-    relabel_hist<<<L.ntiles, kThreads, 0, stream>>>(L);
-    relabel_count<<<L.ntiles, kThreads, 0, stream>>>(L);
-    relabel_scan<<<L.nframes, kThreads, 0, stream>>>(L);
-    relabel_assign<<<L.ntiles, kThreads, 0, stream>>>(L);
-    relabel_apply<<<L.ntiles, kThreads, 0, stream>>>(L);
-    return cudaGetLastError();
+    cudaError_t e = launch_dependent(relabel_zero, L.ntiles, L, stream);
+    if (e == cudaSuccess) e = launch_dependent(relabel_hist, L.ntiles, L, stream);
+    if (e == cudaSuccess) e = launch_dependent(relabel_count, L.ntiles, L, stream);
+    if (e == cudaSuccess) e = launch_dependent(relabel_scan, L.nframes, L, stream);
+    if (e == cudaSuccess) e = launch_dependent(relabel_assign, L.ntiles, L, stream);
+    if (e == cudaSuccess) e = launch_dependent(relabel_apply, L.ntiles, L, stream);
+    return e;
 }
 
 }  // namespace flic

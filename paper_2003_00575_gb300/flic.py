@@ -143,8 +143,8 @@ class Handle:
 
     def close(self) -> None:
         if self.ptr:
-            _check(_lib.flic_destroy(self.ptr))
-            self.ptr = None
+            ptr, self.ptr = self.ptr, None  # freed even when the call reports an error
+            _check(_lib.flic_destroy(ptr))
 
     def __del__(self):
         try:
@@ -240,8 +240,8 @@ class Batch:
 
     def close(self) -> None:
         if self.ptr:
-            _check(_lib.flic_batch_destroy(self.ptr))
-            self.ptr = None
+            ptr, self.ptr = self.ptr, None  # freed even when the call reports an error
+            _check(_lib.flic_batch_destroy(ptr))
 
     def __del__(self):
         try:
@@ -388,8 +388,8 @@ class Server:
 
     def close(self) -> None:
         if self.ptr:
-            _check(_lib.flic_server_destroy(self.ptr))
-            self.ptr = None
+            ptr, self.ptr = self.ptr, None  # freed even when the call reports an error
+            _check(_lib.flic_server_destroy(ptr))
 
     def __del__(self):
         try:

@@ -264,6 +264,30 @@ def run_reference(args, world, rank):
 
 # ------------------------------------------------------------------------ flic arm
 
+def fp64_flip_count(oracle, synth, c4_frames):
+    """Edge decisions of the fp32 test (Eq. 3's constant, the one both the kernels and the
+    oracle evaluate) that the exact double-precision Eq. 2 decides the other way, over every
+    candidate pair of c1-c3 and of the c4 frames; every flip must lie within 1e-5 m of delta."""
+    out = {}
+    sets = {"c1": [synth.config_c1()], "c2": [synth.config_c2()],
+            "c3": [synth.config_c3(with_xyz=False)], "c4": c4_frames}
+    for name, fr in sets.items():
+        pairs = flips = 0
+        dev = 0.0
+        for f in fr:
+            p, n, d = oracle.flips(f.range, f.sensor.elevation, f.sensor.az_step, f.delta, f.skip)
+            pairs += p
+            flips += n
+            dev = max(dev, d)
+        assert flips == 0 or dev < 1e-5, (name, flips, dev)
+        out[name] = {"frames": len(fr), "pairs": pairs, "flips": flips,
+                     "max_abs_d_minus_delta_m": dev}
+    out["bound_m"] = 1e-5
+    out["note"] = ("oracle.flips in the CPU-baseline leg, outside the timed region; the GPU "
+                   "edge bits equal the oracle's bit for bit, so the counts hold for both")
+    return out
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_env()
@@ -653,6 +677,7 @@ def main():
 
     # ---- CPU baseline: the oracle as it stands, 1 thread, all frames once (rank 0, N=1)
     cpu = None
+    fp64_flips = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle  # CPU baseline leg only
         oracle.build()
@@ -675,6 +700,7 @@ def main():
         dt_all = time.perf_counter() - t0
         cpu["all_cores"] = {"value": round(total_px / dt_all / 1e6, 3), "unit": UNIT,
                             "cores": ncores, "frames_per_s": round(len(frames) / dt_all, 2)}
+        fp64_flips = fp64_flip_count(oracle, synth, frames)
 
     for h in handles:
         st = flic.flic_device_status(h)
@@ -706,8 +732,12 @@ def main():
             "segmentation_quality": seg,
             "serving": serving,
             "cpu_baseline": cpu,
+            "fp64_flips": fp64_flips,
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "clock_samples": clocks["samples"],
+            "clock_note": (None if clocks["samples"] >= 10 else
+                           f"only {clocks['samples']} clock samples under load: the timed region "
+                           "was short; the clock record is weak evidence"),
             "gpu_launches": args.steps,
             "wall_s_timed": round(t_wall1 - t_wall0, 3),
             "outputs_sane": bool(sane),

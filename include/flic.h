@@ -413,8 +413,8 @@ double flic_server_clock(void);
  * only use the buffers they are handed: code running inside a host framework whose
  * device memory belongs to its own pool, or plugins that must not call cudaMalloc.  This
  * call needs no handle and allocates nothing: its working memory (the 64-bit per-pixel
- * keys and the boundary tables) lives in static device arrays of fixed size inside
- * libflic, held by every GPU that loads the library until the process exits (about
+ * keys, the boundary tables and a status word) lives in static device arrays of fixed size
+ * inside libflic, held by every GPU that loads the library until the process exits (about
  * 2.1 MiB).
  *   rows, cols   2 <= rows <= FLIC_MAX_ROWS, cols <= FLIC_NOALLOC_MAX_COLS,
  *                rows*cols <= FLIC_NOALLOC_MAX_PIXELS; larger shapes give FLIC_ERR_INVALID
@@ -423,10 +423,15 @@ double flic_server_clock(void);
  *   xyz, n, range_out, point_pixel, stream: as in flic_project (range_out is required)
  * Results are identical to flic_project on a handle of the same geometry.  The first call
  * on each device looks up the static arrays' device addresses (cudaGetSymbolAddress) with
- * that device current, so make it before any stream capture.  Each call copies the tables
- * from host memory on `stream` and clears the keys it uses; all calls share the arrays, so
- * calls that overlap on the GPU (other streams or threads) race and must be serialised by
- * the caller.  Errors: FLIC_ERR_INVALID, FLIC_ERR_UNSUPPORTED, FLIC_ERR_CUDA.
+ * that device current.  Each call copies the tables on `stream` from fixed host arrays
+ * that the next call overwrites (pageable copies, which wait for the work queued earlier
+ * on `stream`), clears the keys it uses and the status word, and — unlike the other
+ * compute calls — returns only when its own work on `stream` has finished, so that a
+ * bounded pixel search that gave up is reported as FLIC_ERR_TIMEOUT.  It can therefore
+ * not be captured into a CUDA graph: a capturing stream gives FLIC_ERR_UNSUPPORTED.  All
+ * calls share the arrays, so calls that overlap on the GPU (other streams or threads) race
+ * and must be serialised by the caller.  Errors: FLIC_ERR_INVALID, FLIC_ERR_UNSUPPORTED,
+ * FLIC_ERR_TIMEOUT, FLIC_ERR_CUDA.
  */
 #define FLIC_NOALLOC_MAX_PIXELS (1 << 18)
 #define FLIC_NOALLOC_MAX_COLS 8192

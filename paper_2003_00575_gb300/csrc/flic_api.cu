@@ -260,38 +260,14 @@ void build_k_tables(int R, const double* elev, double az_step, int S, bool exact
     }
 }
 
-// Projection boundaries: column c starts at azimuth c*az_step; row bands are bounded by
-// midpoints of adjacent sorted beam elevations, outer bands half a spacing beyond.
+// Projection boundaries (flic::build_proj_tables_into) in vectors of the right size.
 bool build_proj_tables(int R, int C, const double* elev, double az_step, std::vector<float>& colb,
                        std::vector<float>& rowb, std::vector<int32_t>& srow) {
     if (R < 2) return false;
     colb.resize((size_t)2 * C);
-    for (int c = 0; c < C; ++c) {
-        double ang = (double)c * az_step;
-        colb[2 * (size_t)c] = (float)std::cos(ang);
-        colb[2 * (size_t)c + 1] = (float)std::sin(ang);
-    }
-    srow.resize(R);
-    for (int r = 0; r < R; ++r) srow[r] = r;
-    std::stable_sort(srow.begin(), srow.end(), [&](int a, int b) { return elev[a] < elev[b]; });
-    for (int i = 1; i < R; ++i)
-        if (!(elev[srow[i]] > elev[srow[i - 1]])) return false;
     rowb.resize((size_t)2 * (R + 1));
-    for (int j = 0; j <= R; ++j) {
-        double m;
-        if (j == 0) {
-            double e0 = elev[srow[0]], e1 = elev[srow[1]];
-            m = e0 - (e1 - e0) / 2.0;
-        } else if (j == R) {
-            double e0 = elev[srow[R - 2]], e1 = elev[srow[R - 1]];
-            m = e1 + (e1 - e0) / 2.0;
-        } else {
-            m = (elev[srow[j - 1]] + elev[srow[j]]) / 2.0;
-        }
-        rowb[2 * (size_t)j] = (float)std::cos(m);
-        rowb[2 * (size_t)j + 1] = (float)std::sin(m);
-    }
-    return true;
+    srow.resize(R);
+    return flic::build_proj_tables_into(R, C, elev, az_step, colb.data(), rowb.data(), srow.data());
 }
 
 template <typename T>
@@ -793,9 +769,10 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
     }
     const int resident = resident_blocks(t.threads, smem, t.ctas_per_sm);
 
-    // the queue: P1 tasks of the frames, largest first; P3 tasks of a frame about two waves
-    // of blocks after its last P1 task (one wave is one P1 task's duration, so a frame's
-    // P3 tasks would arrive just as it finishes), so that they seldom wait
+    // the queue: P1 tasks of the frames, largest first; P3 tasks of a frame p3_delay waves
+    // of blocks after its last P1 task (default 8; one wave is about one P1 task's
+    // duration, so with a delay of one a frame's P3 tasks would arrive just as it
+    // finishes), so that they seldom wait
     std::vector<int> order(nframes);
     for (int i = 0; i < nframes; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int a, int c) {

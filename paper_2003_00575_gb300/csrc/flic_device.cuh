@@ -166,32 +166,4 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32
         : "memory");
 }
 
-// ---- thread-block cluster helpers -----------------------------------------------------
-
-__device__ __forceinline__ unsigned cluster_ctarank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ unsigned cluster_index() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
-    return r;
-}
-
-__device__ __forceinline__ unsigned cluster_count() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
-    return r;
-}
-
-// Every thread of every block of the cluster arrives; release/acquire at cluster scope
-// orders the global-memory writes made before it with the reads made after it.
-__device__ __forceinline__ void cluster_barrier() {
-    asm volatile(
-        "barrier.cluster.arrive.release;\n\t"
-        "barrier.cluster.wait.acquire;" ::: "memory");
-}
-
 }  // namespace flic

@@ -2,6 +2,7 @@
 // Not part of the public ABI (include/flic.h is).
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 
@@ -134,6 +135,49 @@ struct ProjDesc {
     float inv_az_step;      // 1 / az_step, only to seed the column search
     int32_t* status;
 };
+// The projection's boundary tables, written into caller-supplied arrays (no allocation):
+// column c starts at azimuth c*az_step (colb: cols x (cos, sin), fp32 from double); rows are
+// sorted by elevation (srow[j] = the row of the j-th lowest beam, a stable insertion sort)
+// and bounded by the midpoints of adjacent sorted elevations, the outer bands half a spacing
+// beyond their beam (rowb: (rows + 1) x (cos, sin)).  False when rows < 2 or two elevations
+// are equal.  flic_create and flic_project_noalloc both build their tables here.
+inline bool build_proj_tables_into(int R, int C, const double* elev, double az_step, float* colb,
+                                   float* rowb, int32_t* srow) {
+    if (R < 2) return false;
+    for (int c = 0; c < C; ++c) {
+        const double ang = (double)c * az_step;
+        colb[2 * (size_t)c] = (float)std::cos(ang);
+        colb[2 * (size_t)c + 1] = (float)std::sin(ang);
+    }
+    for (int r = 0; r < R; ++r) srow[r] = r;
+    for (int i = 1; i < R; ++i) {
+        const int32_t v = srow[i];
+        int j = i - 1;
+        while (j >= 0 && elev[srow[j]] > elev[v]) {
+            srow[j + 1] = srow[j];
+            --j;
+        }
+        srow[j + 1] = v;
+    }
+    for (int i = 1; i < R; ++i)
+        if (!(elev[srow[i]] > elev[srow[i - 1]])) return false;
+    for (int j = 0; j <= R; ++j) {
+        double m;
+        if (j == 0) {
+            const double e0 = elev[srow[0]], e1 = elev[srow[1]];
+            m = e0 - (e1 - e0) / 2.0;
+        } else if (j == R) {
+            const double e0 = elev[srow[R - 2]], e1 = elev[srow[R - 1]];
+            m = e1 + (e1 - e0) / 2.0;
+        } else {
+            m = (elev[srow[j - 1]] + elev[srow[j]]) / 2.0;
+        }
+        rowb[2 * (size_t)j] = (float)std::cos(m);
+        rowb[2 * (size_t)j + 1] = (float)std::sin(m);
+    }
+    return true;
+}
+
 cudaError_t launch_project(const ProjDesc& P, const float* xyz, int64_t n,
                            unsigned long long* keys, int32_t* point_pixel, cudaStream_t stream);
 cudaError_t launch_decode(const ProjDesc& P, const unsigned long long* keys, float* range_out,

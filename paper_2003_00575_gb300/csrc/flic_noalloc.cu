@@ -4,19 +4,25 @@
 // only touch the buffers it is handed).
 //
 // The projection needs working memory beyond its inputs and outputs: one 64-bit
-// (range, point index) key per pixel, plus the fp32 boundary tables.  Here they live in
-// file-scope static device arrays of a fixed maximum size, which every GPU that loads
-// libflic holds until the process exits:
+// (range, point index) key per pixel, plus the fp32 boundary tables and a status word.
+// Here they live in file-scope static device arrays of a fixed maximum size, which every
+// GPU that loads libflic holds until the process exits:
 //   keys         kNoAllocMaxPixels x 8 B = 2 MiB
-//   column table 2 x kNoAllocMaxCols floats, row table 2 x (rows + 1) floats, row order.
+//   column table 2 x kNoAllocMaxCols floats, row table 2 x (rows + 1) floats, row order,
+//   status       one int32 (a bounded search that gave up)
 // All calls share these arrays and they keep the last call's contents; each call clears
-// the keys it uses before projecting.  Calls whose work overlaps on the GPU (two streams,
-// two host threads) race on the shared arrays and must be serialised by the caller.
+// the keys it uses and the status word before projecting.  Calls whose work overlaps on
+// the GPU (two streams, two host threads) race on the shared arrays and must be
+// serialised by the caller.
 //
 // In host code the arrays' names are host-side stand-ins, not device addresses, so their
 // device addresses are looked up with cudaGetSymbolAddress on the first call on each
-// device (with that device current) and cached.  That first call should therefore come
-// before any stream capture.
+// device (with that device current) and cached.
+//
+// The tables are uploaded from fixed host arrays that every call overwrites, so the call
+// cannot be captured into a CUDA graph (a replay would read whatever those arrays hold
+// then): it refuses a capturing stream.  It also waits for its own work at the end, which
+// lets it report a bounded search that gave up as FLIC_ERR_TIMEOUT.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -37,6 +43,7 @@ static __device__ __align__(256) unsigned long long g_keys[kNoAllocMaxPixels];
 static __device__ __align__(256) float g_colb[2 * kNoAllocMaxCols];
 static __device__ __align__(256) float g_rowb[2 * (kNoAllocMaxRows + 1)];
 static __device__ __align__(256) int32_t g_srow[kNoAllocMaxRows];
+static __device__ __align__(256) int32_t g_status;
 
 namespace {
 
@@ -46,6 +53,7 @@ struct DevicePtrs {
     float* colb = nullptr;
     float* rowb = nullptr;
     int32_t* srow = nullptr;
+    int32_t* status = nullptr;
 };
 
 std::mutex g_mu;
@@ -63,46 +71,6 @@ flic_status na_fail(flic_status st, const char* fmt, ...) {
     va_end(ap);
     flic::set_last_error(msg);  // read back with flic_last_error()
     return st;
-}
-
-// Projection boundaries (same definition as flic_create's tables): column c starts at
-// azimuth c*az_step; row bands are bounded by midpoints of adjacent sorted beam
-// elevations, the outer bands half a spacing beyond their beam.  In-place insertion sort,
-// no allocation.
-bool build_tables(int R, int C, const double* elev, double az_step) {
-    if (R < 2) return false;
-    for (int c = 0; c < C; ++c) {
-        double ang = (double)c * az_step;
-        h_colb[2 * c] = (float)std::cos(ang);
-        h_colb[2 * c + 1] = (float)std::sin(ang);
-    }
-    for (int r = 0; r < R; ++r) h_srow[r] = r;
-    for (int i = 1; i < R; ++i) {
-        int32_t v = h_srow[i];
-        int j = i - 1;
-        while (j >= 0 && elev[h_srow[j]] > elev[v]) {
-            h_srow[j + 1] = h_srow[j];
-            --j;
-        }
-        h_srow[j + 1] = v;
-    }
-    for (int i = 1; i < R; ++i)
-        if (!(elev[h_srow[i]] > elev[h_srow[i - 1]])) return false;
-    for (int j = 0; j <= R; ++j) {
-        double m;
-        if (j == 0) {
-            double e0 = elev[h_srow[0]], e1 = elev[h_srow[1]];
-            m = e0 - (e1 - e0) / 2.0;
-        } else if (j == R) {
-            double e0 = elev[h_srow[R - 2]], e1 = elev[h_srow[R - 1]];
-            m = e1 + (e1 - e0) / 2.0;
-        } else {
-            m = (elev[h_srow[j - 1]] + elev[h_srow[j]]) / 2.0;
-        }
-        h_rowb[2 * j] = (float)std::cos(m);
-        h_rowb[2 * j + 1] = (float)std::sin(m);
-    }
-    return true;
 }
 
 flic_status cuda_err(cudaError_t e, const char* what) {
@@ -131,6 +99,12 @@ extern "C" flic_status flic_project_noalloc(int32_t rows, int32_t cols, const do
     if (e != cudaSuccess) return cuda_err(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return na_fail(FLIC_ERR_UNSUPPORTED, "device ordinal too large");
     cudaStream_t s = (cudaStream_t)stream;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(s, &cap)) != cudaSuccess) return cuda_err(e, "cudaStreamIsCapturing");
+    if (cap != cudaStreamCaptureStatusNone)
+        return na_fail(FLIC_ERR_UNSUPPORTED,
+                       "flic_project_noalloc cannot be captured: its tables come from host "
+                       "arrays that later calls overwrite");
 
     std::lock_guard<std::mutex> lock(g_mu);
     DevicePtrs& d = g_dev[dev];
@@ -138,11 +112,12 @@ extern "C" flic_status flic_project_noalloc(int32_t rows, int32_t cols, const do
         if ((e = cudaGetSymbolAddress((void**)&d.keys, g_keys)) != cudaSuccess ||
             (e = cudaGetSymbolAddress((void**)&d.colb, g_colb)) != cudaSuccess ||
             (e = cudaGetSymbolAddress((void**)&d.rowb, g_rowb)) != cudaSuccess ||
-            (e = cudaGetSymbolAddress((void**)&d.srow, g_srow)) != cudaSuccess)
+            (e = cudaGetSymbolAddress((void**)&d.srow, g_srow)) != cudaSuccess ||
+            (e = cudaGetSymbolAddress((void**)&d.status, g_status)) != cudaSuccess)
             return cuda_err(e, "cudaGetSymbolAddress");
         d.ready = true;
     }
-    if (!build_tables(rows, cols, elevation, az_step))
+    if (!flic::build_proj_tables_into(rows, cols, elevation, az_step, h_colb, h_rowb, h_srow))
         return na_fail(FLIC_ERR_UNSUPPORTED, "flic_project_noalloc: elevations must be distinct");
     // pageable host source: each copy returns once the host data has been staged
     if ((e = cudaMemcpyAsync(d.colb, h_colb, sizeof(float) * 2 * (size_t)cols,
@@ -150,7 +125,8 @@ extern "C" flic_status flic_project_noalloc(int32_t rows, int32_t cols, const do
         (e = cudaMemcpyAsync(d.rowb, h_rowb, sizeof(float) * 2 * (size_t)(rows + 1),
                              cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(d.srow, h_srow, sizeof(int32_t) * (size_t)rows,
-                             cudaMemcpyHostToDevice, s)) != cudaSuccess)
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemsetAsync(d.status, 0, sizeof(int32_t), s)) != cudaSuccess)
         return cuda_err(e, "table upload");
     flic::ProjDesc P{};
     P.colb = d.colb;
@@ -159,10 +135,18 @@ extern "C" flic_status flic_project_noalloc(int32_t rows, int32_t cols, const do
     P.rows = rows;
     P.cols = cols;
     P.inv_az_step = (float)(1.0 / az_step);
-    P.status = nullptr;
+    P.status = d.status;
     // launch_project clears the keys of this frame (0xff: empty) before projecting
     if ((e = flic::launch_project(P, xyz, n, d.keys, point_pixel, s)) != cudaSuccess ||
         (e = flic::launch_decode(P, d.keys, range_out, s)) != cudaSuccess)
         return cuda_err(e, "launch");
+    int32_t st = 0;
+    if ((e = cudaMemcpyAsync(&st, d.status, sizeof(int32_t), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return cuda_err(e, "completion");
+    if (st != 0)
+        return na_fail(FLIC_ERR_TIMEOUT,
+                       "flic_project_noalloc: a bounded pixel search gave up; the pixel map is "
+                       "not valid");
     return FLIC_OK;
 }

@@ -56,3 +56,18 @@ def test_source_hash_follows_the_kernel_sources(tmp_path, monkeypatch):
 def test_peak():
     peak, kind = bench.load_peak()
     assert kind in ("measured", "fallback") and 1000.0 < peak < 20000.0
+
+
+def test_fp64_flip_count_structure_and_bound():
+    """The bench's FP64 flip record: per set the candidate pairs, the flips and the largest
+    |D - delta| of a flip, every flip within the 1e-5 m bound."""
+    import oracle
+    import bench
+    from paper_2003_00575_gb300 import synth
+    fr = synth.config_c4(3)
+    r = bench.fp64_flip_count(oracle, synth, fr)
+    assert r["c4"]["frames"] == 3 and r["c4"]["pairs"] > 0
+    for name in ("c1", "c2", "c3", "c4"):
+        rec = r[name]
+        assert 0 <= rec["flips"] <= rec["pairs"]
+        assert rec["flips"] == 0 or rec["max_abs_d_minus_delta_m"] < r["bound_m"]

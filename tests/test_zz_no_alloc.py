@@ -1,9 +1,10 @@
 """flic_project_noalloc, the projection entry point for callers that cannot allocate
 device memory (for example code inside a host framework whose GPU memory belongs to its
 own pool).  It keeps its working memory in static arrays inside libflic, so these tests
-check, through the C ABI, that its results equal flic_project's bit for bit on two calls
-in a row (the second over a different, smaller frame, so leftovers of the first call
-would show), and that oversized frames are refused with a clear message.
+check, through the C ABI, that its results equal flic_project's and the oracle's bit for
+bit on two calls in a row (the second over a different, smaller frame, so leftovers of the
+first call would show), that oversized frames are refused with a clear message, and that a
+capturing stream is refused (its tables come from host arrays the next call overwrites).
 
 This file is collected last on purpose: if it fails, a run that stops at the first
 failure has already run every other test."""
@@ -14,6 +15,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+import oracle  # noqa: E402
 from paper_2003_00575_gb300 import synth  # noqa: E402
 
 pytestmark = pytest.mark.gpu
@@ -64,6 +66,10 @@ def test_no_alloc_matches_flic_project_on_two_calls_in_a_row(flic):
         np.testing.assert_array_equal(got_p, want_p)
         np.testing.assert_array_equal(got_r.view(np.uint32), want_r.view(np.uint32))
         assert (got_p >= 0).mean() > 0.9
+        s = f.sensor
+        r_o, pix_o, _ = oracle.project(f.xyz, s.rows, s.cols, s.elevation, s.az_step)
+        np.testing.assert_array_equal(got_p, pix_o)
+        np.testing.assert_array_equal(got_r.view(np.uint32), r_o.reshape(-1).view(np.uint32))
 
 
 def test_no_alloc_refuses_frames_beyond_its_static_size(flic):
@@ -74,3 +80,18 @@ def test_no_alloc_refuses_frames_beyond_its_static_size(flic):
                                        out.data_ptr(), None, None)
     assert st == flic.FLIC_ERR_INVALID
     assert b"static limits" in flic._lib.flic_last_error()
+
+
+def test_no_alloc_refuses_a_capturing_stream(flic):
+    s = synth.c5_sensors()[1]
+    elev = np.ascontiguousarray(s.elevation, dtype=np.float64)
+    out = torch.empty(s.rows * s.cols, dtype=torch.float32, device="cuda")
+    side = torch.cuda.Stream()
+    x = torch.zeros(4, device="cuda")
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        x.add_(1.0)
+        st = flic._lib.flic_project_noalloc(s.rows, s.cols, elev.ctypes.data, float(s.az_step),
+                                           None, 0, out.data_ptr(), None, side.cuda_stream)
+    assert st == flic.FLIC_ERR_UNSUPPORTED
+    assert b"captured" in flic._lib.flic_last_error()

@@ -362,7 +362,12 @@ flic_status flic_debug_set_iter_limit(flic_handle h, int32_t limit);
  *   Starts one dispatcher thread.  Each stream has two batch objects: a batch too small
  *   to give every SM one 16384-pixel strip, launched while no other stream has a batch in
  *   flight, is labelled with 2048-pixel strips (lower latency); under load, and for
- *   larger batches, the batch default is used.  Errors: INVALID, OOM, CUDA.
+ *   larger batches, the batch default is used.  Each batch object reserves the shared
+ *   memory of its largest sensor, so every mix of sensors has one launch shape, and is
+ *   launched once at creation (on zeroed slots), so that no CUDA graph is captured while
+ *   frames are served; creation synchronises.  A batch's clouds are projected by one
+ *   launch per step (keys cleared, points projected, range images decoded) and their
+ *   labels scattered by one more.  Errors: INVALID, OOM, CUDA.
  * flic_server_submit — queue one frame; returns at once:
  *   sensor, kind    sensor index; kind 0 = range image (host_in: rows*cols fp32),
  *                   kind 1 = point cloud (host_in: n*3 fp32 xyz, n <= max_points)

@@ -163,6 +163,7 @@ struct flic_batch_ctx {
     int max_frames = 0;
     int max_tasks = 0;
     int device = 0;
+    size_t min_smem = 0;  // launches reserve at least this much (flic::batch_reserve_smem)
     flic::FrameDesc* h_frames = nullptr;  // pinned staging
     flic::Task* h_tasks = nullptr;
     flic::FrameDesc* d_frames = nullptr;
@@ -767,6 +768,7 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
         total_strips += plans[i].nstrips;
         b->h_frames[i] = frame_desc(h, ranges[i], labels[i], plans[i]);
     }
+    smem = std::max(smem, b->min_smem);
     const int resident = resident_blocks(t.threads, smem, t.ctas_per_sm);
 
     // the queue: P1 tasks of the frames, largest first; P3 tasks of a frame p3_delay waves
@@ -1137,6 +1139,49 @@ flic_status flic_filter_relabel_batch(flic_batch b, const flic_handle* hs,
 }
 
 }  // extern "C"
+
+flic_status flic::batch_reserve_smem(flic_batch b, const flic_handle* hs, int n) {
+    if (!b || (n > 0 && !hs)) return fail(FLIC_ERR_INVALID, "NULL argument");
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        StripPlan pl;
+        if (!hs[i] || !plan_frame(hs[i]->R, hs[i]->C, hs[i]->S, b->tune.px_per_cta,
+                                  b->tune.max_strips, &pl))
+            return fail(FLIC_ERR_UNSUPPORTED, "frame %d does not fit the batch's strips", i);
+        smem = std::max(smem, pl.smem);
+    }
+    if (b->pending) cudaEventSynchronize(b->kernel_done);
+    b->min_smem = smem;
+    clear_graphs(b);
+    return FLIC_OK;
+}
+
+flic_status flic::proj_item(flic_handle h, const float* xyz, int64_t n, float* range_out,
+                            int32_t* point_pixel, const int32_t* labels, int32_t* point_labels,
+                            flic::ProjItem* out) {
+    if (!h || !out) return fail(FLIC_ERR_INVALID, "NULL argument");
+    if (!h->proj_ok)
+        return fail(FLIC_ERR_UNSUPPORTED,
+                    "projection needs rows >= 2, distinct elevations and cols*az_step = 2 pi");
+    if (n < 0 || n >= ((int64_t)1 << 31)) return fail(FLIC_ERR_INVALID, "bad point count");
+    flic::ProjItem it{};
+    it.P.colb = h->d_colb;
+    it.P.rowb = h->d_rowb;
+    it.P.srow = h->d_srow;
+    it.P.rows = h->R;
+    it.P.cols = h->C;
+    it.P.inv_az_step = h->inv_az_step;
+    it.P.status = h->d_status;
+    it.xyz = xyz;
+    it.point_pixel = point_pixel;
+    it.keys = h->d_keys;
+    it.range_out = range_out ? range_out : h->d_range;
+    it.labels = labels;
+    it.point_labels = point_labels;
+    it.n = (int32_t)n;
+    *out = it;
+    return FLIC_OK;
+}
 
 flic_status flic::clone_handle(flic_handle h, flic_handle* out, int* rows, int* cols) {
     if (!h) return fail(FLIC_ERR_INVALID, "NULL handle");

@@ -182,6 +182,30 @@ cudaError_t launch_project(const ProjDesc& P, const float* xyz, int64_t n,
                            unsigned long long* keys, int32_t* point_pixel, cudaStream_t stream);
 cudaError_t launch_decode(const ProjDesc& P, const unsigned long long* keys, float* range_out,
                           cudaStream_t stream);
+
+// Many clouds projected (and later scattered) by one launch per kernel: every item is one
+// cloud with its own handle's tables and key scratch (items passed as kernel parameters).
+struct ProjItem {
+    ProjDesc P;                   // the handle's tables, shape and status word
+    const float* xyz;             // n x 3
+    int32_t* point_pixel;         // n
+    unsigned long long* keys;     // rows x cols, the handle's scratch
+    float* range_out;             // rows x cols
+    const int32_t* labels;        // rows x cols (scatter)
+    int32_t* point_labels;        // n (scatter)
+    int32_t n;
+};
+constexpr int kProjBatchItems = 96;
+struct ProjBatch {
+    int32_t nitems;
+    int32_t max_n;                // largest point count of the items
+    int32_t max_px;               // largest pixel count of the items
+    ProjItem item[kProjBatchItems];
+};
+// keys cleared, points projected, range images decoded: three launches for all items
+cudaError_t launch_project_batch(const ProjBatch& B, cudaStream_t stream);
+// every item's point labels from its pixel labels: one launch
+cudaError_t launch_scatter_batch(const ProjBatch& B, cudaStream_t stream);
 // Sets the thread-local message returned by flic_last_error().
 void set_last_error(const char* msg);
 
@@ -190,6 +214,13 @@ void set_last_error(const char* msg);
 namespace flic {
 // A new handle with the same geometry, threshold, skip, flags and tuning as h.
 flic_status clone_handle(flic_handle h, flic_handle* out, int* rows, int* cols);
+// Launches of batch object b reserve the shared memory of the largest of these frames (with
+// b's tuning), so that every mix of them uses one launch shape and one captured graph.
+flic_status batch_reserve_smem(flic_batch b, const flic_handle* hs, int n);
+// The projection item of one cloud on handle h (FLIC_ERR_UNSUPPORTED when h cannot project).
+flic_status proj_item(flic_handle h, const float* xyz, int64_t n, float* range_out,
+                      int32_t* point_pixel, const int32_t* labels, int32_t* point_labels,
+                      ProjItem* out);
 
 cudaError_t launch_scatter(const int32_t* labels, int64_t npix, const int32_t* point_pixel,
                            int64_t n, int32_t* point_labels, cudaStream_t stream);

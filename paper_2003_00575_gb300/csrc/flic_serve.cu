@@ -4,10 +4,11 @@
 // One dispatcher thread admits them into free frame slots — device memory reserved per
 // sensor at creation, so admission is by device memory — and, whenever one of its
 // streams ("lanes") is idle, launches everything admitted as one batch on that lane:
-// host-to-device copies, the projection of each cloud (flic_project on the slot's own
-// handle, so concurrent projections never share scratch), one flic_label_batch for all
-// frames, the scatter of each cloud's labels, device-to-host copies, and a host callback
-// that time-stamps completion.  While one lane's batch runs, requests that arrive are
+// host-to-device copies, the projection of all clouds of the batch (one launch each to
+// clear the keys, project the points and decode the range images, every cloud on its
+// slot's own handle, so concurrent projections never share scratch), one flic_label_batch
+// for all frames, one scatter launch for all clouds, device-to-host copies, and a host
+// callback that time-stamps completion.  While one lane's batch runs, requests that arrive are
 // admitted and launched on the next lane, so batches overlap on the device.  Each frame's
 // results equal the single-frame calls: the kernels decide every pixel and point the same
 // way whatever else shares the launch.
@@ -70,6 +71,7 @@ struct Lane {
     flic_batch batch_small = nullptr;
     bool busy = false;
     Flight f;
+    std::vector<flic::ProjBatch> proj;  // the batch's projection items (launch parameters)
 };
 
 struct Sensor {
@@ -222,6 +224,35 @@ extern "C" flic_status flic_server_create(const flic_handle* sensors, int32_t ns
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         s->small_px = (size_t)std::max(nsm, 1) * 16384;  // one batch-sized strip per SM
     }
+    // one launch shape per batch object whatever the sensor mix, captured now: every batch
+    // object reserves the shared memory of its largest sensor and labels one slot of each
+    // sensor once (zeroed readings), so that no graph is captured while frames are served
+    {
+        std::vector<flic_handle> hs;
+        std::vector<const float*> rs;
+        std::vector<int32_t*> ls;
+        for (const Sensor& sn : s->sensors) {
+            const Slot& sl = s->slots[sn.free_slots.front()];
+            hs.push_back(sl.h);
+            rs.push_back(sl.d_range);
+            ls.push_back(sl.d_labels);
+            cudaMemset(sl.d_range, 0, (size_t)sn.rows * sn.cols * 4);
+        }
+        const int n = (int)hs.size();
+        flic_status st = FLIC_OK;
+        for (Lane& ln : s->lanes) {
+            for (flic_batch b : {ln.batch, ln.batch_small}) {
+                if (st == FLIC_OK) st = flic::batch_reserve_smem(b, hs.data(), n);
+                if (st == FLIC_OK)
+                    st = flic_label_batch(b, hs.data(), rs.data(), ls.data(), n, ln.stream);
+            }
+            if (st == FLIC_OK && cudaStreamSynchronize(ln.stream) != cudaSuccess) st = FLIC_ERR_CUDA;
+        }
+        if (st != FLIC_OK) {
+            free_server(s);
+            return srv_fail(st, "flic_server_create: warm-up launch failed");
+        }
+    }
     s->dispatcher = std::thread(dispatch_loop, s);
     *out = s;
     return FLIC_OK;
@@ -249,6 +280,9 @@ void launch(flic_server_ctx* s, Lane& ln, std::vector<Request>& take, std::vecto
         if (status == FLIC_OK && x != FLIC_OK) status = x;
     };
     auto cu = [&](cudaError_t e) { note(e == cudaSuccess ? FLIC_OK : FLIC_ERR_CUDA); };
+    // the clouds' projection and scatter items, in launches of up to kProjBatchItems
+    std::vector<flic::ProjBatch>& pb = ln.proj;
+    pb.clear();
     for (int i = 0; i < n; ++i) {
         const Request& q = f.reqs[i];
         const Slot& sl = s->slots[f.slots[i]];
@@ -259,12 +293,26 @@ void launch(flic_server_ctx* s, Lane& ln, std::vector<Request>& take, std::vecto
         } else {
             if (q.n > 0)
                 cu(cudaMemcpyAsync(sl.d_xyz, q.in, (size_t)q.n * 12, cudaMemcpyHostToDevice, st));
-            note(flic_project(sl.h, sl.d_xyz, q.n, sl.d_range, sl.d_pix, st));
+            if (pb.empty() || pb.back().nitems == flic::kProjBatchItems) {
+                pb.emplace_back();
+                pb.back().nitems = pb.back().max_n = pb.back().max_px = 0;
+            }
+            flic::ProjBatch& b = pb.back();
+            flic::ProjItem& it = b.item[b.nitems];
+            const flic_status ps = flic::proj_item(sl.h, sl.d_xyz, q.n, sl.d_range, sl.d_pix,
+                                                   sl.d_labels, sl.d_plab, &it);
+            note(ps);
+            if (ps == FLIC_OK) {
+                ++b.nitems;
+                b.max_n = std::max(b.max_n, it.n);
+                b.max_px = std::max(b.max_px, sn.rows * sn.cols);
+            }
         }
         hs[i] = sl.h;
         rs[i] = sl.d_range;
         ls[i] = sl.d_labels;
     }
+    for (const flic::ProjBatch& b : pb) cu(flic::launch_project_batch(b, st));
     size_t px = 0;
     for (int i = 0; i < n; ++i) {
         const Sensor& sn = s->sensors[f.reqs[i].sensor];
@@ -277,6 +325,7 @@ void launch(flic_server_ctx* s, Lane& ln, std::vector<Request>& take, std::vecto
         if (&o != &ln && o.busy) alone = false;
     note(flic_label_batch(alone && px < s->small_px ? ln.batch_small : ln.batch, hs.data(),
                           rs.data(), ls.data(), n, st));
+    for (const flic::ProjBatch& b : pb) cu(flic::launch_scatter_batch(b, st));
     for (int i = 0; i < n; ++i) {
         const Request& q = f.reqs[i];
         const Slot& sl = s->slots[f.slots[i]];
@@ -285,7 +334,6 @@ void launch(flic_server_ctx* s, Lane& ln, std::vector<Request>& take, std::vecto
             cu(cudaMemcpyAsync(q.out, sl.d_labels, (size_t)sn.rows * sn.cols * 4,
                                cudaMemcpyDeviceToHost, st));
         } else if (q.n > 0) {
-            note(flic_scatter(sl.h, sl.d_labels, sl.d_pix, q.n, sl.d_plab, st));
             cu(cudaMemcpyAsync(q.out, sl.d_plab, (size_t)q.n * 4, cudaMemcpyDeviceToHost, st));
         }
     }

@@ -14,6 +14,7 @@ scheduled times and reads the completion records.  Per step it reports p50/p99 l
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import time
@@ -51,17 +52,25 @@ def poisson_schedule(rate: float, seconds: float, nsensors: int, seed: int):
 
 def summarize(records, t0: float, t1: float) -> dict:
     """Latency percentiles (ms) and throughput of completion records (dicts or structs
-    with t_submit, t_done, batch_size, status)."""
+    with t_submit, t_launch, t_done, batch_size, status).  The latency splits into the wait
+    in the admission queue (submission to the launch of the frame's batch) and the service
+    time (the batch's launch to its results in host memory: enqueueing, copies, kernels)."""
     if not records:
         return {"completed": 0}
     lat = np.array([(r.t_done - r.t_submit) * 1e3 for r in records])
+    wait = np.array([(r.t_launch - r.t_submit) * 1e3 for r in records])
+    svc = np.array([(r.t_done - r.t_launch) * 1e3 for r in records])
     bs = np.array([r.batch_size for r in records])
     ok = sum(1 for r in records if r.status == 0)
     span = max(t1 - t0, 1e-9)
+
+    def pc(x, q):
+        return round(float(np.percentile(x, q)), 3)
     return {"completed": len(records), "ok": ok, "frames_per_s": round(len(records) / span, 1),
-            "latency_ms_p50": round(float(np.percentile(lat, 50)), 3),
-            "latency_ms_p99": round(float(np.percentile(lat, 99)), 3),
+            "latency_ms_p50": pc(lat, 50), "latency_ms_p99": pc(lat, 99),
             "latency_ms_max": round(float(lat.max()), 3),
+            "queue_ms_p50": pc(wait, 50), "queue_ms_p99": pc(wait, 99),
+            "service_ms_p50": pc(svc, 50), "service_ms_p99": pc(svc, 99),
             "mean_batch": round(float(bs.mean()), 2)}
 
 
@@ -103,20 +112,29 @@ class FramePool:
 
 
 def run_step(flic, srv, pool: FramePool, rate: float, seconds: float, seed: int) -> dict:
+    """Submit a Poisson schedule at its times and summarize the completions.  The garbage
+    collector is off while the schedule is paced: a full collection over the growing list
+    of completion records stalls this thread for tens of milliseconds, and the frames due
+    meanwhile would then arrive as one burst that the schedule never had."""
     sched = poisson_schedule(rate, seconds, len(pool.inputs), seed)
     records, rejected = [], 0
-    t_start = time.perf_counter()
-    c0 = flic.flic_server_clock()
-    for i, (t, s, kind) in enumerate(sched):
-        while time.perf_counter() - t_start < t:
-            pass
-        x, y = pool.pick(s, kind)
-        if flic.flic_server_submit(srv, s, kind, x, y, i) != flic.FLIC_OK:
-            rejected += 1
-        if i % 64 == 0:
-            records += flic.flic_server_poll(srv)
-    flic.flic_server_drain(srv, 120.0)
-    records += flic.flic_server_poll(srv)
+    gc.collect()
+    gc.disable()
+    try:
+        t_start = time.perf_counter()
+        c0 = flic.flic_server_clock()
+        for i, (t, s, kind) in enumerate(sched):
+            while time.perf_counter() - t_start < t:
+                pass
+            x, y = pool.pick(s, kind)
+            if flic.flic_server_submit(srv, s, kind, x, y, i) != flic.FLIC_OK:
+                rejected += 1
+            if i % 64 == 0:
+                records += flic.flic_server_poll(srv)
+        flic.flic_server_drain(srv, 120.0)
+        records += flic.flic_server_poll(srv)
+    finally:
+        gc.enable()
     c1 = max([r.t_done for r in records], default=c0)
     out = summarize(records, c0, c1)
     out.update({"rate_offered": round(rate, 1), "submitted": len(sched), "rejected": rejected})
@@ -132,6 +150,8 @@ def main(argv=None):
     p.add_argument("--streams", type=int, default=2)
     p.add_argument("--max-batch", type=int, default=256)
     p.add_argument("--mem-gb", type=float, default=4.0)
+    p.add_argument("--only-top", type=int, default=0,
+                   help="run only the last N rate steps (each seconds/steps long)")
     args = p.parse_args(argv)
     import torch
     from . import flic, synth
@@ -143,7 +163,10 @@ def main(argv=None):
                                   max_batch=args.max_batch, mem_budget=int(args.mem_gb * 2**30))
     warm = run_step(flic, srv, pool, 200.0, 0.5, 999)  # first launches capture graphs
     steps = []
-    for i, rate in enumerate(rate_steps(args.lo, args.hi, args.steps)):
+    rates = rate_steps(args.lo, args.hi, args.steps)
+    for i, rate in enumerate(rates):
+        if args.only_top and i < len(rates) - args.only_top:
+            continue
         r = run_step(flic, srv, pool, rate, args.seconds / args.steps, 1000 + i)
         steps.append(r)
         print(json.dumps(r), flush=True)

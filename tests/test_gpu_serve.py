@@ -150,3 +150,34 @@ def test_served_with_ground_extraction(flic):
             want = oracle.scatter(oracle.label_ground(r, s.elevation, s.az_step, 0.5, 3, True,
                                                       theta, 1.7), pix)
         np.testing.assert_array_equal(y.numpy(), want, err_msg=f.name)
+
+
+def test_batch_of_more_clouds_than_one_projection_launch(flic):
+    """104 clouds held and released as one batch: their projection and scatter run as two
+    launches of items each (96 + 8); every cloud's point labels equal its alone result."""
+    s = synth.c5_sensors()[0]
+    h = flic.flic_create(s.rows, s.cols, s.elevation, s.az_step, 0.5, 3)
+    clouds = [synth.c5_frame(s, 7000 + j, as_cloud=True) for j in range(4)]
+    want = [_alone(flic, f) for f in clouds]
+    mp = max(f.xyz.shape[0] for f in clouds)
+    budget = 110 * (s.rows * s.cols * 8 + mp * 20)
+    srv = flic.flic_server_create([h], [mp], nstreams=1, max_batch=128, mem_budget=budget)
+    try:
+        ins = [torch.from_numpy(f.xyz.reshape(-1)).pin_memory() for f in clouds]
+        outs = []
+        flic.flic_server_hold(srv, True)
+        for i in range(104):
+            y = torch.full((clouds[i % 4].xyz.shape[0],), -5, dtype=torch.int32).pin_memory()
+            assert flic.flic_server_submit(srv, 0, 1, ins[i % 4], y, i) == flic.FLIC_OK
+            outs.append(y)
+        flic.flic_server_hold(srv, False)
+        flic.flic_server_drain(srv, 60.0)
+        recs = flic.flic_server_poll(srv)
+    finally:
+        srv.close()
+        h.close()
+    assert sorted(r.tag for r in recs) == list(range(104))
+    assert all(r.status == 0 for r in recs)
+    assert max(r.batch_size for r in recs) > 96
+    for i, y in enumerate(outs):
+        np.testing.assert_array_equal(y.numpy(), want[i % 4], err_msg=str(i))

@@ -30,9 +30,12 @@ def test_poisson_schedule_seeded_rates_and_mix():
 
 
 def test_summarize_percentiles():
-    recs = [types.SimpleNamespace(t_submit=0.0, t_done=i / 1000.0, batch_size=2, status=0)
-            for i in range(1, 101)]
+    # frame i waits i/2 ms for its launch and takes i/2 ms of service
+    recs = [types.SimpleNamespace(t_submit=0.0, t_launch=i / 2000.0, t_done=i / 1000.0,
+                                  batch_size=2, status=0) for i in range(1, 101)]
     s = serve.summarize(recs, 0.0, 1.0)
     assert s["completed"] == 100 and s["frames_per_s"] == 100.0
     assert abs(s["latency_ms_p50"] - 50.5) < 1e-6 and s["latency_ms_max"] == 100.0
+    assert abs(s["queue_ms_p50"] - 25.25) < 1e-6 and abs(s["service_ms_p50"] - 25.25) < 1e-6
+    assert s["queue_ms_p99"] <= s["latency_ms_p99"]
     assert serve.summarize([], 0, 1) == {"completed": 0}

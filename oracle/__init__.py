@@ -11,7 +11,10 @@ Functions and the passages they follow:
               true angle between the rays of a row (exact_ray)
   pred        Eq. 2/3 squared distance against delta (§III-B)
   edges       per-pixel edge bits for offsets 1..S (§III-B-1 binary images, §III-B-2)
-  label       BFS connected-component labelling, min-index labels (§III-B-1)
+  label       BFS connected-component labelling, min-index labels (§III-B-1); with
+              diagonal=True also the diagonal Map Connections (§III-B-2)
+  tables_diag Eq. 3 constants of the diagonal pairs (r, c)-(r+k, c+-k): the squared distance
+              of the two unit rays, in double
   flips       FP64 Eq. 2 decision vs the fp32 one
   project     spherical projection of xyz into the range image (§I)
   scatter     labels back to points (§I, Fig. 1)
@@ -83,6 +86,10 @@ def _load():
         lib.oracle_scatter.restype = None
         lib.oracle_ground.argtypes = [i32, i32, P, P, f64, f64, P]
         lib.oracle_ground.restype = None
+        lib.oracle_tables_diag.argtypes = [i32, P, f64, i32, P]
+        lib.oracle_tables_diag.restype = None
+        lib.oracle_label_diag.argtypes = [i32, i32, P, P, P, P, i32, f32, i32, P]
+        lib.oracle_label_diag.restype = i64
         _lib = lib
         return lib
 
@@ -140,17 +147,35 @@ def edges(range_img, elevation, az_step: float, delta: float, skip: int, wrap: b
     return mask
 
 
+def tables_diag(elevation, az_step: float, skip: int):
+    """Kd float32 [rows, skip]: Eq. 3's constant of the diagonal pair (r, c)-(r+k, c+-k),
+    2 - 2 cos(alpha) with alpha the angle between the two beams' rays (0 where r+k >= rows)."""
+    elev = _f64(elevation)
+    R = elev.shape[0]
+    kd = np.zeros((R, skip), np.float32)
+    _load().oracle_tables_diag(R, _ptr(elev), float(az_step), skip, _ptr(kd))
+    return kd
+
+
 def label(range_img, elevation, az_step: float, delta: float, skip: int, wrap: bool = True,
-          exact_ray: bool = False, lattice: bool = False):
+          exact_ray: bool = False, lattice: bool = False, diagonal: bool = False):
     """int32 [rows, cols] labels: min linear index of the component, -1 for invalid.
-    lattice: the sparse Map Connection of §III-B-2 (see edges)."""
+    lattice: the sparse Map Connection of §III-B-2 (see edges); diagonal: the diagonal Map
+    Connections (r, c)-(r+k, c+-k), k = 1..skip, as well (not with lattice)."""
     rng = _f32(range_img)
     R, C = rng.shape
     kv, kh = tables(elevation, az_step, skip, exact_ray)
     out = np.empty((R, C), np.int32)
-    n = _load().oracle_label_ex(R, C, _ptr(rng), _ptr(kv), _ptr(kh), skip,
-                                float(np.float32(delta)), int(bool(wrap)), int(bool(lattice)),
-                                _ptr(out))
+    if diagonal:
+        if lattice:
+            raise ValueError("diagonal Map Connections are not combined with the sparse map")
+        kd = tables_diag(elevation, az_step, skip)
+        n = _load().oracle_label_diag(R, C, _ptr(rng), _ptr(kv), _ptr(kh), _ptr(kd), skip,
+                                      float(np.float32(delta)), int(bool(wrap)), _ptr(out))
+    else:
+        n = _load().oracle_label_ex(R, C, _ptr(rng), _ptr(kv), _ptr(kh), skip,
+                                    float(np.float32(delta)), int(bool(wrap)),
+                                    int(bool(lattice)), _ptr(out))
     if n < 0:
         raise MemoryError("oracle_label: out of memory")
     return out

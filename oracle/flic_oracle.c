@@ -24,6 +24,11 @@
  *   oracle_edges_ex,  the same with the paper's sparse Map Connection (§III-B-2): besides
  *   oracle_label_ex   the direct neighbours, only every S-th point in each direction is
  *                     joined, to the S-th point further on (a sub-lattice map)
+ *   oracle_tables_diag, oracle_label_diag
+ *                     Map Connections along the diagonals of the range image (§III-B-2,
+ *                     "MCs along the main diagonal"): besides the row and column offsets
+ *                     1..S, pixel (r, c) is joined to (r+k, c+k) and (r+k, c-k), k = 1..S,
+ *                     with the constant of the true angle between the two beams
  */
 #include <float.h>
 #include <math.h>
@@ -540,4 +545,86 @@ done:
     free(thi);
     free(se);
     free(ce);
+}
+
+
+/*
+ * Diagonal Map Connections (§III-B-2, "MCs along the main diagonal of the range image").
+ * The pair (r, c)-(r+k, c+-k) joins two beams k rows and k columns apart; its alpha is the
+ * angle between their rays, so Eq. 3's constant is K = 2 - 2 cos(alpha) = |u1 - u2|^2 for
+ * the unit rays u1 = (cos e1, 0, sin e1) and u2 = (cos e2 cos(k step), cos e2 sin(k step),
+ * sin e2), e1 = elev[r], e2 = elev[r+k] (the same for +k and -k columns).  Computed in
+ * double as that squared distance, rounded once.  Kd[r*S + k-1], 0 when r+k >= R.
+ */
+void oracle_tables_diag(int32_t R, const double* elev, double az_step, int32_t S, float* Kd) {
+    for (int32_t r = 0; r < R; ++r) {
+        for (int32_t k = 1; k <= S; ++k) {
+            float kd = 0.0f;
+            if (r + k < R) {
+                const double e1 = elev[r], e2 = elev[r + k], ph = (double)k * az_step;
+                const double dx = cos(e1) - cos(e2) * cos(ph);
+                const double dy = -cos(e2) * sin(ph);
+                const double dz = sin(e1) - sin(e2);
+                kd = (float)(dx * dx + dy * dy + dz * dz);
+            }
+            Kd[r * S + (k - 1)] = kd;
+        }
+    }
+}
+
+/*
+ * oracle_label with the diagonal Map Connections as well: breadth-first search in raster
+ * order (§III-B-1), the candidate neighbours of (r, c) being (r, c+-k) and (r+-k, c) as in
+ * oracle_label, and the four diagonal ones (r+-k, c+-k), k = 1..S (columns mod C with
+ * wrap, else inside the frame); a diagonal pair uses Kd of its upper row.
+ */
+int64_t oracle_label_diag(int32_t R, int32_t C, const float* range, const float* Kv,
+                          const float* Kh, const float* Kd, int32_t S, float delta, int32_t wrap,
+                          int32_t* labels) {
+    int64_t N = (int64_t)R * C;
+    float delta2 = oracle_delta2(delta);
+    int32_t* queue = (int32_t*)malloc((size_t)(N > 0 ? N : 1) * sizeof(int32_t));
+    if (!queue) return -1;
+    for (int64_t p = 0; p < N; ++p) labels[p] = -1;
+    int64_t ncomp = 0;
+    for (int64_t p0 = 0; p0 < N; ++p0) {
+        if (labels[p0] != -1 || !oracle_valid(range[p0])) continue;
+        ++ncomp;
+        int64_t head = 0, tail = 0;
+        labels[p0] = (int32_t)p0;
+        queue[tail++] = (int32_t)p0;
+        while (head < tail) {
+            int32_t u = queue[head++];
+            int32_t ur = u / C, uc = u % C;
+            float a = range[u];
+            for (int32_t k = 1; k <= S; ++k) {
+                /* dr, dc in {-1, 0, 1} x {-1, 0, 1} without (0, 0): axis and diagonal */
+                for (int dr = -1; dr <= 1; ++dr) {
+                    for (int dc = -1; dc <= 1; ++dc) {
+                        if (dr == 0 && dc == 0) continue;
+                        int32_t vr = ur + dr * k;
+                        int32_t vc = uc + dc * k;
+                        if (vr < 0 || vr >= R) continue;
+                        if (vc < 0 || vc >= C) {
+                            if (!wrap) continue;
+                            vc = ((vc % C) + C) % C;
+                        }
+                        int32_t v = vr * C + vc;
+                        if (labels[v] != -1) continue;
+                        float b = range[v];
+                        if (!oracle_valid(b)) continue;
+                        int32_t top = dr > 0 ? ur : vr;
+                        float K = dr == 0 ? Kh[ur * S + k - 1]
+                                : dc == 0 ? Kv[top * S + k - 1] : Kd[top * S + k - 1];
+                        if (oracle_pred(a, b, K, delta2)) {
+                            labels[v] = (int32_t)p0;
+                            queue[tail++] = v;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    free(queue);
+    return ncomp;
 }

@@ -81,6 +81,13 @@ typedef enum {
  * multiples of skip (the pair's left or upper end; its column before any wrap), offsets
  * 2..skip-1 not at all.  Without it every pixel uses every offset 1..skip. */
 #define FLIC_FLAG_SUBLATTICE 0x4u
+/* Map Connections along the diagonals (§III-B-2, "MCs along the main diagonal"): besides
+ * the row and column offsets, pixel (r,c) is joined to (r+k,(c+k) mod cols) and
+ * (r+k,(c-k) mod cols) for k = 1..skip (no wrap: inside the frame only), with the Eq. 3
+ * constant of the true angle between the two beams' rays, K = |u1 - u2|^2 for the unit rays
+ * at (elev[r], 0) and (elev[r+k], k az_step), computed in double and rounded once.  Not
+ * combined with FLIC_FLAG_SUBLATTICE.  flic_edges reports the row and column pairs only. */
+#define FLIC_FLAG_DIAGONAL 0x8u
 
 /* Largest frame the labeller accepts: rows * cols <= FLIC_MAX_PIXELS, rows <= FLIC_MAX_ROWS.
  * A frame is split into at most 64 full-height column strips of at most 32768 (padded)
@@ -126,6 +133,14 @@ flic_status flic_destroy(flic_handle h);
  *            are 0.  Either pointer may be NULL.
  */
 flic_status flic_get_tables(flic_handle h, float* kv, float* kh);
+
+/*
+ * flic_get_diag_table — copy the handle's diagonal constants (FLIC_FLAG_DIAGONAL, §III-B-2)
+ * to host memory: kd, host, rows*skip floats, [r][k-1] = the constant of the pairs
+ * (r,c)-(r+k,c+-k), 0 where r+k >= rows.  FLIC_ERR_INVALID when the handle was created
+ * without the flag.
+ */
+flic_status flic_get_diag_table(flic_handle h, float* kd);
 
 /*
  * flic_edges — the neighbour test alone (Eq. 2/3 with Map Connections, §III-B-2):

@@ -71,7 +71,8 @@ int pow2_log2_ceil(int x) {
 // at most max_strips strips, widths a multiple of 4 (aligned vector access), every strip
 // at least `skip` wide when there are several (so an edge crosses at most one border),
 // and rows * pitch <= kMaxPaddedStrip with pitch = next power of two >= max(width, 32).
-bool plan_frame(int R, int C, int S, int px_target, int max_strips, StripPlan* out) {
+bool plan_frame(int R, int C, int S, int px_target, int max_strips, StripPlan* out,
+                bool diag = false) {
     int n0 = std::max(1, std::min(max_strips, ceil_div(std::max(1, R * C), std::max(1, px_target))));
     // preferred strip count first, then more strips, then fewer; for each count a few
     // widths, so that a narrow last strip can be avoided
@@ -91,7 +92,7 @@ bool plan_frame(int R, int C, int S, int px_target, int max_strips, StripPlan* o
             }
             int sh = std::max(5, pow2_log2_ceil(W));
             if ((long long)R << sh > kMaxPaddedStrip) continue;
-            size_t smem = flic::strip_smem_bytes(R, sh, W, S);
+            size_t smem = flic::strip_smem_bytes(R, sh, W, S, diag);
             if (smem > flic::kMaxDynSmem) continue;
             out->nstrips = n_eff;
             out->strip_w = W;
@@ -136,7 +137,8 @@ struct flic_ctx {
     int device = 0;
     float* d_kv = nullptr;
     float* d_kh = nullptr;
-    std::vector<float> h_kv, h_kh;
+    float* d_kd = nullptr;  // diagonal Map Connections (FLIC_FLAG_DIAGONAL), else nullptr
+    std::vector<float> h_kv, h_kh, h_kd;
     std::vector<double> elev;  // the creation arguments, for flic::clone_handle
     bool proj_ok = false;
     float* d_colb = nullptr;
@@ -220,6 +222,7 @@ flic::FrameDesc frame_desc(const flic_ctx* h, const float* range, int32_t* label
     f.labels = labels;
     f.kv = h->d_kv;
     f.kh = h->d_kh;
+    f.kd = h->d_kd;
     f.status = h->d_status;
     f.rows = h->R;
     f.cols = h->C;
@@ -261,6 +264,22 @@ void build_k_tables(int R, const double* elev, double az_step, int S, bool exact
     }
 }
 
+// Eq. 3 constants of the diagonal pairs (r, c)-(r+k, c+-k): 2 - 2 cos(alpha) with alpha the
+// angle between the two rays, as the squared distance |u1 - u2|^2 of the unit rays at
+// (elev[r], 0) and (elev[r+k], k * az_step), in double, rounded once (0 where r+k >= R).
+std::vector<float> build_kd_table(int R, const double* elev, double az_step, int S) {
+    std::vector<float> kd((size_t)R * S, 0.0f);
+    for (int r = 0; r < R; ++r)
+        for (int k = 1; k <= S && r + k < R; ++k) {
+            const double e1 = elev[r], e2 = elev[r + k], ph = (double)k * az_step;
+            const double x = std::cos(e1) - std::cos(e2) * std::cos(ph);
+            const double y = std::cos(e2) * std::sin(ph);
+            const double z = std::sin(e1) - std::sin(e2);
+            kd[(size_t)r * S + k - 1] = (float)(x * x + y * y + z * z);
+        }
+    return kd;
+}
+
 // Projection boundaries (flic::build_proj_tables_into) in vectors of the right size.
 bool build_proj_tables(int R, int C, const double* elev, double az_step, std::vector<float>& colb,
                        std::vector<float>& rowb, std::vector<int32_t>& srow) {
@@ -286,6 +305,7 @@ void free_ctx(flic_ctx* h) {
     if (!h) return;
     cudaFree(h->d_kv);
     cudaFree(h->d_kh);
+    cudaFree(h->d_kd);
     cudaFree(h->d_colb);
     cudaFree(h->d_rowb);
     cudaFree(h->d_srow);
@@ -300,7 +320,8 @@ void free_ctx(flic_ctx* h) {
 
 flic_status replan(flic_ctx* h) {
     StripPlan pl;
-    if (!plan_frame(h->R, h->C, h->S, h->tune.px_per_cta, h->tune.max_strips, &pl))
+    if (!plan_frame(h->R, h->C, h->S, h->tune.px_per_cta, h->tune.max_strips, &pl,
+                    h->d_kd != nullptr))
         return fail(FLIC_ERR_UNSUPPORTED, "frame %dx%d (skip %d) does not fit %d strips",
                     h->R, h->C, h->S, h->tune.max_strips);
     h->plan = pl;
@@ -336,8 +357,11 @@ flic_status flic_create_ex(int32_t rows, int32_t cols, const double* elevation, 
     if (!(delta > 0.0f) || !std::isfinite(delta))
         return fail(FLIC_ERR_INVALID, "delta must be positive and finite");
     if (skip < 1 || skip > FLIC_MAX_SKIP) return fail(FLIC_ERR_INVALID, "skip must be 1..%d", FLIC_MAX_SKIP);
-    if (flags & ~(FLIC_FLAG_NO_WRAP | FLIC_FLAG_EXACT_RAY | FLIC_FLAG_SUBLATTICE))
+    if (flags & ~(FLIC_FLAG_NO_WRAP | FLIC_FLAG_EXACT_RAY | FLIC_FLAG_SUBLATTICE |
+                  FLIC_FLAG_DIAGONAL))
         return fail(FLIC_ERR_INVALID, "unknown flags 0x%x", flags);
+    if ((flags & FLIC_FLAG_DIAGONAL) && (flags & FLIC_FLAG_SUBLATTICE))
+        return fail(FLIC_ERR_INVALID, "diagonal Map Connections are not combined with the sparse map");
 
     flic_ctx* h = new flic_ctx();
     h->R = rows;
@@ -360,6 +384,10 @@ flic_status flic_create_ex(int32_t rows, int32_t cols, const double* elevation, 
                    h->h_kh);
     if ((st = upload(&h->d_kv, h->h_kv, "Kv table")) != FLIC_OK) { free_ctx(h); return st; }
     if ((st = upload(&h->d_kh, h->h_kh, "Kh table")) != FLIC_OK) { free_ctx(h); return st; }
+    if (flags & FLIC_FLAG_DIAGONAL) {
+        h->h_kd = build_kd_table(rows, elevation, az_step, skip);
+        if ((st = upload(&h->d_kd, h->h_kd, "Kd table")) != FLIC_OK) { free_ctx(h); return st; }
+    }
     std::vector<int32_t> zero(1, 0);
     if ((st = upload(&h->d_status, zero, "status word")) != FLIC_OK) { free_ctx(h); return st; }
     std::vector<int32_t> zeros(flic::counter_ints(1), 0);
@@ -403,6 +431,13 @@ flic_status flic_get_tables(flic_handle h, float* kv, float* kh) {
     if (!h) return fail(FLIC_ERR_INVALID, "NULL handle");
     if (kv) std::memcpy(kv, h->h_kv.data(), sizeof(float) * h->h_kv.size());
     if (kh) std::memcpy(kh, h->h_kh.data(), sizeof(float) * h->h_kh.size());
+    return FLIC_OK;
+}
+
+flic_status flic_get_diag_table(flic_handle h, float* kd) {
+    if (!h || !kd) return fail(FLIC_ERR_INVALID, "NULL argument");
+    if (h->h_kd.empty()) return fail(FLIC_ERR_INVALID, "the handle has no diagonal Map Connections");
+    std::memcpy(kd, h->h_kd.data(), sizeof(float) * h->h_kd.size());
     return FLIC_OK;
 }
 
@@ -761,7 +796,7 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
     int total_strips = 0;
     for (int i = 0; i < nframes; ++i) {
         const flic_ctx* h = hs[i];
-        if (!plan_frame(h->R, h->C, h->S, t.px_per_cta, t.max_strips, &plans[i]))
+        if (!plan_frame(h->R, h->C, h->S, t.px_per_cta, t.max_strips, &plans[i], h->d_kd != nullptr))
             return fail(FLIC_ERR_UNSUPPORTED, "frame %d (%dx%d) does not fit %d strips", i, h->R,
                         h->C, t.max_strips);
         smem = std::max(smem, plans[i].smem);
@@ -1146,7 +1181,7 @@ flic_status flic::batch_reserve_smem(flic_batch b, const flic_handle* hs, int n)
     for (int i = 0; i < n; ++i) {
         StripPlan pl;
         if (!hs[i] || !plan_frame(hs[i]->R, hs[i]->C, hs[i]->S, b->tune.px_per_cta,
-                                  b->tune.max_strips, &pl))
+                                  b->tune.max_strips, &pl, hs[i]->d_kd != nullptr))
             return fail(FLIC_ERR_UNSUPPORTED, "frame %d does not fit the batch's strips", i);
         smem = std::max(smem, pl.smem);
     }

@@ -22,6 +22,8 @@ struct FrameDesc {
     int32_t* labels;      // rows*cols, device (output and global union-find forest)
     const float* kv;      // rows*skip, Eq. 3 constants of vertical pairs (upper row)
     const float* kh;      // rows*skip, Eq. 3 constants of horizontal pairs
+    const float* kd;      // rows*skip, Eq. 3 constants of diagonal pairs (upper row), or
+                          // nullptr when the frame has no diagonal Map Connections
     int32_t* status;      // device error word of the owning handle
     int32_t rows, cols, skip;
     float delta2;         // delta*delta in fp32
@@ -75,12 +77,12 @@ struct LabelLaunch {
 // Shared memory (bytes) one block needs for a strip of `rows` x `width` columns with
 // local pitch 1 << pitch_log2 and skip S: the staged readings (rows x (width + S) rounded
 // up to 4, later reused as the parent array, rows x pitch ints) and 2S + 1 ballot words
-// per 32-column row segment.
-inline size_t strip_smem_bytes(int rows, int pitch_log2, int width, int skip) {
+// per 32-column row segment (twice that with the diagonal Map Connections).
+inline size_t strip_smem_bytes(int rows, int pitch_log2, int width, int skip, bool diag = false) {
     size_t pitch = size_t(1) << pitch_log2;
     size_t rp = (size_t(width) + size_t(skip) + 3) & ~size_t(3);
     size_t a = size_t(rows) * (rp > pitch ? rp : pitch) * 4;
-    size_t words = size_t(rows) * (pitch / 32) * (2 * size_t(skip) + 1) * 4;
+    size_t words = size_t(rows) * (pitch / 32) * (2 * size_t(skip) + 1) * 4 * (diag ? 2 : 1);
     return a + words + 64;
 }
 

@@ -63,6 +63,7 @@ struct Strip {
     int32_t* labels;
     const float* kv;
     const float* kh;
+    const float* kd;   // diagonal constants, nullptr: no diagonal Map Connections
     int32_t* status;
     int R, C, S;
     float delta2;
@@ -82,6 +83,7 @@ struct Carve {
     float* stage;      // R x RP staged readings; reused as the parent array (R x P)
     int* par;
     unsigned* words;   // R x P/32 row segments x (2S + 1) ballot words
+    unsigned* dwords;  // the same for the diagonal Map Connections (when there are any)
 };
 
 __device__ __forceinline__ Carve carve(unsigned char* base, const Strip& s) {
@@ -91,6 +93,7 @@ __device__ __forceinline__ Carve carve(unsigned char* base, const Strip& s) {
     c.stage = reinterpret_cast<float*>(base);
     c.par = reinterpret_cast<int*>(base);
     c.words = reinterpret_cast<unsigned*>(base + 4 * (size_t)a_words);
+    c.dwords = c.words + (size_t)(s.R << (s.sh - 5)) * (2 * s.S + 1);
     return c;
 }
 
@@ -120,6 +123,14 @@ struct Words {
 template <int S>
 __device__ __forceinline__ Words<S> words_of(const Strip& s, const Carve& sm) {
     return Words<S>{sm.words, s.R << (s.sh - 5)};
+}
+
+// The diagonal words of a strip, in the same layout: [k] edge from the pixel to the pixel
+// k rows down and k columns right, [S + k] k rows down and k columns left (k = 1..S);
+// [0] is unused.
+template <int S>
+__device__ __forceinline__ Words<S> dwords_of(const Strip& s, const Carve& sm) {
+    return Words<S>{sm.dwords, s.R << (s.sh - 5)};
 }
 
 // Bits 0..c of a word (c in 0..31).
@@ -285,6 +296,30 @@ __device__ __forceinline__ void mask_chunk(const Strip& s, const float* row, int
     }
 }
 
+// The diagonal words of the same chunk (§III-B-2, Map Connections along the diagonals):
+// edges (r, c)-(r+k, c+k) and (r, c)-(r+k, c-k) whose far end lies inside the strip (the
+// boundary merge tests the others), with the constant kd of the pair's upper row.
+template <int S, bool kInterior>
+__device__ __forceinline__ void diag_chunk(const Strip& s, const float* row, int c, int down,
+                                           const float (&kd)[S], unsigned w0,
+                                           unsigned (&d)[2 * S + 1]) {
+    const bool in = kInterior || c < s.W;
+    const float a = in ? row[c] : 0.0f;
+    d[0] = 0u;
+#pragma unroll
+    for (int k = 1; k <= S; ++k) {
+        const bool vin = kInterior || (in && k <= down);
+        const bool rin = vin && (kInterior || c + k < s.W);
+        const bool lin = vin && c >= k;
+        const float br = rin ? row[c + k + k * s.RP] : 0.0f;
+        const float bl = lin ? row[c - k + k * s.RP] : 0.0f;
+        float dr, dl;
+        edge_d2_pair(a, br, bl, kd[k - 1], kd[k - 1], dr, dl);
+        d[k] = __ballot_sync(kFull, (br > 0.0f) & (dr <= s.delta2)) & w0;
+        d[S + k] = __ballot_sync(kFull, (bl > 0.0f) & (dl <= s.delta2)) & w0;
+    }
+}
+
 // 1b. The sparse Map Connection (§III-B-2, every S-th point joined at offset S), applied to
 //     the ballot words of the whole strip (one thread per row segment): offsets 2..S-1
 //     dropped, offset S kept only where the row and the global column are multiples of S.
@@ -314,22 +349,25 @@ __device__ void lattice_words(const Strip& s, const Carve& sm) {
 }
 
 // 1. The ballot words of every row segment from the staged readings (a warp per row).
-template <int S>
+template <int S, bool D>
 __device__ void mask_rows(const Strip& s, const Carve& sm) {
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
     const int nwarps = blockDim.x >> 5;
     const Words<S> wd = words_of<S>(s, sm);
+    const Words<S> dd = dwords_of<S>(s, sm);
     for (int r = warp; r < s.R; r += nwarps) {
-        float kh[S], kv[S];
+        float kh[S], kv[S], kd[S];
 #pragma unroll
         for (int k = 0; k < S; ++k) {
             kh[k] = __ldg(s.kh + r * S + k);
             kv[k] = __ldg(s.kv + r * S + k);
+            kd[k] = D ? __ldg(s.kd + r * S + k) : 0.0f;
         }
         const int down = min(S, s.R - 1 - r);  // vertical offsets that stay in the frame
         const float* row = sm.stage + r * s.RP;
         unsigned* out = wd.w + (size_t)(r << (s.sh - 5)) * Words<S>::NP;
+        unsigned* dout = dd.w + (size_t)(r << (s.sh - 5)) * Words<S>::NP;
         // chunks with cs + 32 + S <= W and S rows below are interior
         const int interior = down == S && s.W >= S ? ((s.W - S) >> 5) << 5 : 0;
         int cs = 0;
@@ -339,12 +377,24 @@ __device__ void mask_rows(const Strip& s, const Carve& sm) {
             // every lane stores the same word to the same address: one write
 #pragma unroll
             for (int p = 0; p <= 2 * S; ++p) out[(cs >> 5) * Words<S>::NP + p] = w[p];
+            if constexpr (D) {
+                unsigned d[2 * S + 1];
+                diag_chunk<S, true>(s, row, cs + lane, down, kd, w[0], d);
+#pragma unroll
+                for (int p = 0; p <= 2 * S; ++p) dout[(cs >> 5) * Words<S>::NP + p] = d[p];
+            }
         }
         for (; cs < s.W; cs += 32) {
             unsigned w[2 * S + 1];
             mask_chunk<S, false>(s, row, cs + lane, down, kh, kv, w);
 #pragma unroll
             for (int p = 0; p <= 2 * S; ++p) out[(cs >> 5) * Words<S>::NP + p] = w[p];
+            if constexpr (D) {
+                unsigned d[2 * S + 1];
+                diag_chunk<S, false>(s, row, cs + lane, down, kd, w[0], d);
+#pragma unroll
+                for (int p = 0; p <= 2 * S; ++p) dout[(cs >> 5) * Words<S>::NP + p] = d[p];
+            }
         }
     }
 }
@@ -450,30 +500,100 @@ __device__ __forceinline__ void for_each_pair(const Strip& s, const Words<S>& wd
     }
 }
 
+// The diagonal pairs of runs (x, y), y < x, whose upper end lies in row segment u (row r):
+// the edges (r, c)-(r+k, c+k) and (r, c)-(r+k, c-k) of its diagonal words.  An edge that a
+// vertical offset-k edge and a run of row r or of row r+k already join is dropped — on
+// smooth surfaces nearly all of them; of consecutive edges joining the same two runs only
+// the first is taken.  Far ends in the next or previous segment of row r+k lie inside the
+// strip (the edge pass records no other).
+template <int S, class Op>
+__device__ __forceinline__ void for_each_diag_pair(const Strip& s, const Words<S>& wd,
+                                                   const Words<S>& dd, int u, Op op) {
+    const int nsl = s.sh - 5;
+    const int NS = 1 << nsl;
+    const int r = u >> nsl;
+    const unsigned h1 = wd(1, u);
+    const unsigned rs = wd.starts(u);
+    const int base = u << 5;
+#pragma unroll
+    for (int k = 1; k <= S; ++k) {
+        if (r + k >= s.R) break;
+        unsigned dr = dd(k, u), dl = dd(S + k, u);
+        if (!(dr | dl)) continue;
+        const int ud = u + k * NS;  // the same segment of row r + k
+        const unsigned vk = wd(S + k, u);
+        const unsigned hd = wd(1, ud);
+        // bit c: columns c .. c + k form one run (row r: sa, row r + k: sb)
+        unsigned sa = ~0u, sb = ~0u;
+#pragma unroll
+        for (int j = 0; j < k; ++j) {
+            sa &= h1 >> j;
+            sb &= hd >> j;
+        }
+        dr &= ~((vk & sb) | (sa & (vk >> k)));
+        dl &= ~((vk & (sb << k)) | ((sa & vk) << k));
+        const unsigned rsd = wd.starts(ud);
+        int la = -1, lb = -1;
+        while (dr) {
+            const int c = __ffs(dr) - 1;
+            dr &= dr - 1u;
+            const int t = c + k;
+            const int a = base + top_bit(rs & upto(c));
+            const int b = t < 32 ? (ud << 5) + top_bit(rsd & upto(t))
+                                 : ((ud + 1) << 5) + top_bit(wd.starts(ud + 1) & upto(t - 32));
+            if (a != la || b != lb) {
+                op(b, a);
+                la = a;
+                lb = b;
+            }
+        }
+        la = lb = -1;
+        while (dl) {
+            const int c = __ffs(dl) - 1;
+            dl &= dl - 1u;
+            const int t = c - k;
+            const int a = base + top_bit(rs & upto(c));
+            const int b = t >= 0 ? (ud << 5) + top_bit(rsd & upto(t))
+                                 : ((ud - 1) << 5) + top_bit(wd.starts(ud - 1) & upto(t + 32));
+            if (a != la || b != lb) {
+                op(b, a);
+                la = a;
+                lb = b;
+            }
+        }
+    }
+}
+
 // b. Linking: every run start takes as parent the smallest run that one of its pairs
 //    reaches (shared-memory atomicMin, no finds).  Parents are smaller, so this is a
 //    forest, and most of the strip's structure is in it before any find runs.
-template <int S>
+template <int S, bool D>
 __device__ void link_runs(const Strip& s, const Carve& sm) {
     const Words<S> wd = words_of<S>(s, sm);
+    const Words<S> dd = dwords_of<S>(s, sm);
     const int nsl = s.sh - 5;
     int* par = sm.par;
     for (int u = threadIdx.x; u < wd.n; u += blockDim.x) {
         if (((u & ((1 << nsl) - 1)) << 5) >= s.W) continue;
-        for_each_pair<S>(s, wd, u, [&](int x, int y) { atomicMin(par + slot(x), y); });
+        auto op = [&](int x, int y) { atomicMin(par + slot(x), y); };
+        for_each_pair<S>(s, wd, u, op);
+        if constexpr (D) for_each_diag_pair<S>(s, wd, dd, u, op);
     }
 }
 
 // c. Every pair united (finds with path halving, atomicMin hooking to the smaller root,
 //    retry when a hook loses a race).
-template <int S>
+template <int S, bool D>
 __device__ void unite_runs(const Strip& s, const Carve& sm) {
     const Words<S> wd = words_of<S>(s, sm);
+    const Words<S> dd = dwords_of<S>(s, sm);
     const int nsl = s.sh - 5;
     int* par = sm.par;
     for (int u = threadIdx.x; u < wd.n; u += blockDim.x) {
         if (((u & ((1 << nsl) - 1)) << 5) >= s.W) continue;
-        for_each_pair<S>(s, wd, u, [&](int x, int y) { unite(par, x, y, s); });
+        auto op = [&](int x, int y) { unite(par, x, y, s); };
+        for_each_pair<S>(s, wd, u, op);
+        if constexpr (D) for_each_diag_pair<S>(s, wd, dd, u, op);
     }
 }
 
@@ -552,36 +672,55 @@ __device__ void write_labels(const Strip& s, const Carve& sm) {
 }
 
 // Steps 1 and a to e of a staged strip.
-template <int S>
+template <int S, bool D>
 __device__ void phase1_strip(const Strip& s, const Carve& sm) {
-    mask_rows<S>(s, sm);
+    mask_rows<S, D>(s, sm);
     __syncthreads();  // the staged readings are dead from here on
-    if (s.lattice) {
+    if (!D && s.lattice) {
         lattice_words<S>(s, sm);
         __syncthreads();
     }
     init_runs<S>(s, sm);
     __syncthreads();
-    link_runs<S>(s, sm);
+    link_runs<S, D>(s, sm);
     __syncthreads();
-    unite_runs<S>(s, sm);
+    unite_runs<S, D>(s, sm);
     __syncthreads();
     flatten_runs<S>(s, sm);
     __syncthreads();
     write_labels<S>(s, sm);
 }
 
-__device__ void phase1(const Strip& s, const Carve& sm) {
-    if (s.gnd) phase1_ground(s, sm);
+// The strip pass with the diagonal Map Connections: a function of its own, so that its
+// larger register needs stay out of the code of the plain strip pass.
+__device__ __noinline__ void phase1_diag(const Strip& s, const Carve& sm) {
     switch (s.S) {
-        case 1: phase1_strip<1>(s, sm); break;
-        case 2: phase1_strip<2>(s, sm); break;
-        case 3: phase1_strip<3>(s, sm); break;
-        case 4: phase1_strip<4>(s, sm); break;
-        case 5: phase1_strip<5>(s, sm); break;
-        case 6: phase1_strip<6>(s, sm); break;
-        case 7: phase1_strip<7>(s, sm); break;
-        default: phase1_strip<8>(s, sm); break;
+        case 1: phase1_strip<1, true>(s, sm); break;
+        case 2: phase1_strip<2, true>(s, sm); break;
+        case 3: phase1_strip<3, true>(s, sm); break;
+        case 4: phase1_strip<4, true>(s, sm); break;
+        case 5: phase1_strip<5, true>(s, sm); break;
+        case 6: phase1_strip<6, true>(s, sm); break;
+        case 7: phase1_strip<7, true>(s, sm); break;
+        default: phase1_strip<8, true>(s, sm); break;
+    }
+}
+
+__device__ __forceinline__ void phase1(const Strip& s, const Carve& sm) {
+    if (s.gnd) phase1_ground(s, sm);
+    if (s.kd) {  // with the diagonal Map Connections
+        phase1_diag(s, sm);
+        return;
+    }
+    switch (s.S) {
+        case 1: phase1_strip<1, false>(s, sm); break;
+        case 2: phase1_strip<2, false>(s, sm); break;
+        case 3: phase1_strip<3, false>(s, sm); break;
+        case 4: phase1_strip<4, false>(s, sm); break;
+        case 5: phase1_strip<5, false>(s, sm); break;
+        case 6: phase1_strip<6, false>(s, sm); break;
+        case 7: phase1_strip<7, false>(s, sm); break;
+        default: phase1_strip<8, false>(s, sm); break;
     }
 }
 
@@ -671,6 +810,74 @@ __device__ void border_merge_narrow(const FrameDesc& f, int limit) {
     }
 }
 
+// The diagonal pairs (§III-B-2) that cross border b, at x = the first column right of it
+// (x = cols for the azimuth seam): (r, x-k+j)-(r+k, x+j) down to the right from the last k
+// columns of strip b, (r, x+j)-(r+k, x-k+j) down to the left from the first k columns of
+// the next strip, j = 0..k-1, columns mod cols.  Every strip is at least S wide, so such a
+// pair crosses this border only.
+__device__ void border_merge_diag(const FrameDesc& f, int b, int limit,
+                                  unsigned long long* pair_set) {
+    const int R = f.rows, C = f.cols, S = f.skip;
+    const int c0 = b * f.strip_w;
+    const int x = c0 + min(f.strip_w, C - c0);
+    const int per_row = S * (S + 1);  // (k, j, direction): 2k of them per k
+    for (int t = threadIdx.x; t < R * per_row; t += blockDim.x) {
+        const int r = t / per_row;
+        int q = t - r * per_row;
+        int k = 1;
+        while (q >= 2 * k) {
+            q -= 2 * k;
+            ++k;
+        }
+        if (r + k >= R) continue;
+        const int j = q >> 1;
+        int ca = (q & 1) ? x + j : x - k + j;  // upper end
+        int cb = (q & 1) ? x - k + j : x + j;  // lower end
+        if (ca >= C) ca -= C;                  // the seam (a border past the last column
+        if (cb >= C) cb -= C;                  // exists only with wrap)
+        const float av = load_range_g(f, r, ca);
+        const float bv = load_range_g(f, r + k, cb);
+        if (!(av > 0.0f) || !(bv > 0.0f) ||
+            !edge_pred(av, bv, __ldg(f.kd + r * S + k - 1), f.delta2))
+            continue;
+        const int ga = __ldcg(f.labels + (size_t)r * C + ca);
+        const int gb = __ldcg(f.labels + (size_t)(r + k) * C + cb);
+        if (ga == gb) continue;
+        const unsigned long long key = ((unsigned long long)(unsigned)ga << 32) | (unsigned)gb;
+        const int h = (int)((key * 0x9E3779B97F4A7C15ull) >> 58);
+        if (volatile_load_u64(pair_set + h) == key) continue;
+        int budget = limit;
+        union_global(f.labels, ga, gb, budget);
+        if (budget <= 0) report_timeout(f.status);
+        pair_set[h] = key;
+    }
+}
+
+// The diagonal pairs of a single strip narrower than S that wrap around the seam (the
+// edge pass records those whose far column lies inside the strip).
+__device__ void border_merge_narrow_diag(const FrameDesc& f, int limit) {
+    const int R = f.rows, C = f.cols, S = f.skip;
+    for (int t = threadIdx.x; t < R * C; t += blockDim.x) {
+        const int r = t / C, c = t - r * C;
+        const float a = load_range_g(f, r, c);
+        if (!(a > 0.0f)) continue;
+        for (int k = 1; k <= S && r + k < R; ++k) {
+            for (int dir = -1; dir <= 1; dir += 2) {
+                const int cc = c + dir * k;
+                if (cc >= 0 && cc < C) continue;
+                const int tc = ((cc % C) + C) % C;
+                const float d = load_range_g(f, r + k, tc);
+                if (d > 0.0f && edge_pred(a, d, __ldg(f.kd + r * S + k - 1), f.delta2)) {
+                    int budget = limit;
+                    union_global(f.labels, __ldcg(f.labels + t),
+                                 __ldcg(f.labels + (size_t)(r + k) * C + tc), budget);
+                    if (budget <= 0) report_timeout(f.status);
+                }
+            }
+        }
+    }
+}
+
 __device__ void border_merge(const FrameDesc& f, int b) {
     const int limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
     // root pairs this block has united during this merge (a cache: a collision only
@@ -681,8 +888,10 @@ __device__ void border_merge(const FrameDesc& f, int b) {
     const int W = min(f.strip_w, f.cols - b * f.strip_w);
     if (W < f.skip) {
         border_merge_narrow(f, limit);
+        if (f.kd) border_merge_narrow_diag(f, limit);
         return;
     }
+    if (f.kd) border_merge_diag(f, b, limit, pair_set);
     switch (f.skip) {
         case 1: border_merge_s<1>(f, b, limit, pair_set); break;
         case 2: border_merge_s<2>(f, b, limit, pair_set); break;
@@ -837,6 +1046,7 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
             s.labels = f.labels;
             s.kv = f.kv;
             s.kh = f.kh;
+            s.kd = f.kd;
             s.status = f.status;
             s.R = f.rows;
             s.C = f.cols;

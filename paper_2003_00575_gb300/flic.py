@@ -26,6 +26,7 @@ FLIC_ERR_UNSUPPORTED = 6
 FLIC_FLAG_NO_WRAP = 1
 FLIC_FLAG_EXACT_RAY = 2
 FLIC_FLAG_SUBLATTICE = 4
+FLIC_FLAG_DIAGONAL = 8
 FLIC_HOST_INPUT_READY = 1
 FLIC_MAX_PIXELS = 1 << 21
 FLIC_MAX_ROWS = 512
@@ -47,6 +48,7 @@ SIGNATURES = {
     "flic_create_ex": (_I32, [_I32, _I32, _P, _F64, _F32, _I32, _U32, _P]),
     "flic_destroy": (_I32, [_P]),
     "flic_get_tables": (_I32, [_P, _P, _P]),
+    "flic_get_diag_table": (_I32, [_P, _P]),
     "flic_edges": (_I32, [_P, _P, _P, _P]),
     "flic_label": (_I32, [_P, _P, _P, _P]),
     "flic_project": (_I32, [_P, _P, _I64, _P, _P, _P]),
@@ -159,15 +161,17 @@ def flic_abi_version() -> int:
 
 
 def flic_create(rows: int, cols: int, elevation, az_step: float, delta: float, skip: int,
-                wrap: bool = True, exact_ray: bool = False, lattice: bool = False) -> Handle:
+                wrap: bool = True, exact_ray: bool = False, lattice: bool = False,
+                diagonal: bool = False) -> Handle:
     """lattice: the paper's sparse Map Connection (every skip-th point joined at offset
-    skip, direct neighbours everywhere) instead of offsets 1..skip from every pixel."""
+    skip, direct neighbours everywhere) instead of offsets 1..skip from every pixel;
+    diagonal: the diagonal Map Connections (r, c)-(r+k, c+-k), k = 1..skip, as well."""
     elev = np.ascontiguousarray(elevation, dtype=np.float64)
     if elev.shape != (rows,):
         raise ValueError("elevation must have one entry per row")
     out = ctypes.c_void_p()
     flags = ((0 if wrap else FLIC_FLAG_NO_WRAP) | (FLIC_FLAG_EXACT_RAY if exact_ray else 0)
-             | (FLIC_FLAG_SUBLATTICE if lattice else 0))
+             | (FLIC_FLAG_SUBLATTICE if lattice else 0) | (FLIC_FLAG_DIAGONAL if diagonal else 0))
     _check(_lib.flic_create_ex(rows, cols, elev.ctypes.data, float(az_step), float(delta), skip,
                                flags, ctypes.byref(out)))
     return Handle(out.value, rows, cols, skip, float(np.float32(delta)), wrap)
@@ -182,6 +186,12 @@ def flic_get_tables(h: Handle):
     kh = np.zeros((h.rows, h.skip), np.float32)
     _check(_lib.flic_get_tables(h.ptr, kv.ctypes.data, kh.ctypes.data))
     return kv, kh
+
+
+def flic_get_diag_table(h: Handle):
+    kd = np.zeros((h.rows, h.skip), np.float32)
+    _check(_lib.flic_get_diag_table(h.ptr, kd.ctypes.data))
+    return kd
 
 
 def flic_plan_info(h: Handle) -> dict:

@@ -99,3 +99,13 @@ def test_strip_planner_invariants(lib_path, seed):
     rp = (W + S + 3) // 4 * 4
     assert 4 * R * max(rp, P) + 4 * R * (P // 32) * (2 * S + 1) + 64 == p["smem"]
     assert p["smem"] <= 227 * 1024 - 1024
+
+
+def test_diagonal_and_sparse_map_flags_are_exclusive():
+    """The flags are checked before any device work, so this runs without a GPU."""
+    import numpy as np
+    from paper_2003_00575_gb300 import flic
+    with pytest.raises(flic.FlicError) as e:
+        flic.flic_create(4, 16, np.radians([3.0, 1.0, -1.0, -3.0]), 2 * np.pi / 16, 0.5, 2,
+                         lattice=True, diagonal=True)
+    assert e.value.status == flic.FLIC_ERR_INVALID

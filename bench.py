@@ -21,6 +21,10 @@ Reported (one JSON line on rank 0):
                pixel) / mean launch time vs the measured HBM copy bandwidth
   projection   flic_project + flic_label + flic_scatter on the 128x2048 occlusion frame
                with 262,144 xyz points
+  projection_batch  a c5 batch of 96 clouds (30k-260k points each) through
+               flic_project_batch + flic_label_batch + flic_scatter_batch, with the HBM
+               rooflines of the batched projection and scatter
+  edges        flic_edges (the 16-byte word pass) on a 512x4096 frame, S = 3 and 5, GB/s
   serving      a short sweep of the continuous-batching server (four Poisson sensors,
                half of the frames as xyz clouds) at 1,000 / 5,000 / 20,000 frames/s:
                p50/p99 latency from submission to labels in host memory
@@ -286,6 +290,129 @@ def fp64_flip_count(oracle, synth, c4_frames):
     out["note"] = ("oracle.flips in the CPU-baseline leg, outside the timed region; the GPU "
                    "edge bits equal the oracle's bit for bit, so the counts hold for both")
     return out
+
+
+def host_ahead(torch, stream, us: float = 1000.0) -> None:
+    """Occupy the stream with a spin kernel of about `us` microseconds so that the launches
+    enqueued after it are all queued on the device before the first timing event runs:
+    events then time device work back to back, not the host's launch rate."""
+    with torch.cuda.stream(stream):
+        torch.cuda._sleep(int(us * 2000))
+
+
+def edges_section(flic, synth, torch, dev, stream, peak, peak_kind):
+    """flic_edges alone on the largest frame the API takes (512 x 4096 = 2^21 pixels: the
+    c3 range image tiled 4 x 2), 16 frame copies in rotation (201 MB > L2), for S = 3 and
+    5.  Algorithmic bytes: 4 B of range read and 2 B of mask written per pixel."""
+    f3 = synth.config_c3(with_xyz=False)
+    R, C = 512, 4096
+    rimg = np.tile(f3.range, (4, 2))
+    s = synth.make_sensor(R, C, -22.5, 22.5)
+    ncopy, reps = 16, 4
+    rs = [torch.from_numpy(rimg.reshape(-1)).to(dev) for _ in range(ncopy)]
+    ms = [torch.empty(R * C, dtype=torch.int16, device=dev) for _ in range(ncopy)]
+    out = {"workload": f"{R}x{C} (the c3 range image tiled 4 x 2), {ncopy} copies in "
+                       f"rotation ({ncopy * 6 * R * C / 1e6:.0f} MB > L2)",
+           "algorithmic_bytes_per_launch": 6 * R * C}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for S in (3, 5):
+        h = flic.flic_create(R, C, s.elevation, s.az_step, 0.4, S)
+        for i in range(3 * ncopy):
+            flic.flic_edges(h, rs[i % ncopy], ms[i % ncopy], stream)
+        torch.cuda.synchronize()
+        host_ahead(torch, stream, 3000.0)
+        ev[0].record(stream)
+        for i in range(reps * ncopy):
+            flic.flic_edges(h, rs[i % ncopy], ms[i % ncopy], stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        ok = flic.flic_device_status(h) == flic.FLIC_OK
+        h.close()
+        us = ev[0].elapsed_time(ev[1]) * 1e3 / (reps * ncopy)
+        gbs = 6 * R * C / (us * 1e-6) / 1e9
+        out[f"S{S}"] = {"us_per_launch": round(us, 3),
+                        "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak,
+                                     "unit": "GB/s", "frac": round(gbs / peak, 4),
+                                     "traffic": None,
+                                     "peak_source": f"of {peak_kind} (hbm_gbs, burst copy)"},
+                        "status_ok": ok}
+    out["timing"] = (f"{reps * ncopy} back-to-back launches between two CUDA events on the "
+                     "launching stream, all queued behind a spin kernel before the first event "
+                     "(device time, inter-launch gaps included), after 48 warm-up launches")
+    return out
+
+
+def projection_batch_section(flic, synth, torch, dev, stream, peak, peak_kind):
+    """A c5 batch of 96 clouds (24 per serving sensor, 30k-260k points each: 16 distinct
+    clouds, each in 6 separate device buffers) projected by flic_project_batch, labelled
+    by flic_label_batch and scattered by flic_scatter_batch; two such batches in rotation
+    (> L2).  Algorithmic bytes: projection 12 B xyz read + 4 B pixel index written per
+    point and 4 B of range written per pixel; scatter 4 B pixel index + 4 B label read and
+    4 B written per point."""
+    sens = synth.c5_sensors()
+    distinct = [synth.c5_frame(sens[i % 4], 9000 + i, as_cloud=True) for i in range(16)]
+    nb, per = 2, 96
+    batches = []
+    for _ in range(nb):
+        fr = [distinct[i % 16] for i in range(per)]
+        hs = [flic.flic_create(f.sensor.rows, f.sensor.cols, f.sensor.elevation,
+                               f.sensor.az_step, f.delta, f.skip) for f in fr]
+        xyz = [torch.from_numpy(np.ascontiguousarray(f.xyz).reshape(-1)).to(dev) for f in fr]
+        pix = [torch.empty(f.xyz.shape[0], dtype=torch.int32, device=dev) for f in fr]
+        rng = [torch.empty(f.range.size, dtype=torch.float32, device=dev) for f in fr]
+        lab = [torch.empty(f.range.size, dtype=torch.int32, device=dev) for f in fr]
+        plab = [torch.empty_like(p) for p in pix]
+        ca = flic.CloudArgs(hs, xyz, pix, range_out=rng, labels=lab, point_labels=plab)
+        b = flic.flic_batch_create(per)
+        batches.append((hs, ca, b, flic.BatchArgs(hs, rng, lab), xyz, pix, rng, lab, plab))
+    npts = sum(distinct[i % 16].xyz.shape[0] for i in range(per))
+    npx = sum(distinct[i % 16].range.size for i in range(per))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    t = []
+    for rep in range(23):
+        hs, ca, b, ba = batches[rep % nb][:4]
+        host_ahead(torch, stream, 1000.0)
+        ev[0].record(stream)
+        flic.flic_project_batch(ca, stream)
+        ev[1].record(stream)
+        flic.flic_label_batch(b, ba, stream)
+        ev[2].record(stream)
+        flic.flic_scatter_batch(ca, stream)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        if rep >= 3:
+            t.append([ev[0].elapsed_time(ev[1]), ev[1].elapsed_time(ev[2]),
+                      ev[2].elapsed_time(ev[3]), ev[0].elapsed_time(ev[3])])
+    ok = all(flic.flic_device_status(h) == flic.FLIC_OK for bt in batches for h in bt[0])
+    for bt in batches:
+        bt[2].close()
+        for h in bt[0]:
+            h.close()
+    t = np.array(t)
+    med = [float(np.median(t[:, i])) for i in range(4)]
+    pb = 16 * npts + 4 * npx
+    sb = 12 * npts
+
+    def roof(nbytes, ms):
+        gbs = nbytes / (ms * 1e-3) / 1e9
+        return {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(gbs / peak, 4), "traffic": None,
+                "algorithmic_bytes_per_call": nbytes,
+                "peak_source": f"of {peak_kind} (hbm_gbs, burst copy)"}
+
+    return {"workload": f"c5 batch: {per} clouds on the 4 serving sensors, {npts:,} points, "
+                        f"{npx:,} pixels, {nb} batches in rotation",
+            "ms_project_batch": round(med[0], 4), "ms_label_batch": round(med[1], 4),
+            "ms_scatter_batch": round(med[2], 4), "ms_total": round(med[3], 4),
+            "clouds_per_s": round(per / (med[3] * 1e-3), 1),
+            "mpoints_per_s": round(npts / (med[3] * 1e-3) / 1e6, 1),
+            "roofline_project": roof(pb, med[0]), "roofline_scatter": roof(sb, med[2]),
+            "launches": "project: 3 (keys cleared, points projected, ranges decoded); "
+                        "label: 1; scatter: 1 (at most 96 clouds per launch)",
+            "timing": "CUDA events between the calls on the launching stream, the three "
+                      "calls queued behind a spin kernel before the first event (device "
+                      "time); median of 20 after 3 warm-up batches",
+            "status_ok": ok}
 
 
 def main():
@@ -658,6 +785,10 @@ def main():
         "mpoints_per_s": round(cloud.shape[0] / (float(np.median(lp[:, 3])) / 1e3) / 1e6, 1),
     }
     h3.close()
+    edges = edges_section(flic, synth, torch, dev, stream, peak, peak_kind)
+    sane &= edges["S3"]["status_ok"] and edges["S5"]["status_ok"]
+    projection_batch = projection_batch_section(flic, synth, torch, dev, stream, peak, peak_kind)
+    sane &= projection_batch["status_ok"]
 
     # ---- short serving sweep: four Poisson sensors, half clouds (the full one: serve.py)
     serving = None
@@ -727,6 +858,8 @@ def main():
             "e2e": e2e,
             "roofline": roofline,
             "projection": projection,
+            "projection_batch": projection_batch,
+            "edges": edges,
             "cluster_filter": cluster_filter,
             "ground_extraction": ground_extraction,
             "segmentation_quality": seg,

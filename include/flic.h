@@ -175,9 +175,9 @@ flic_status flic_label(flic_handle h, const float* range, int32_t* labels, void*
  * row boundaries are the midpoints between adjacent beam elevations, the outer rows
  * extending half a spacing beyond their beam.  Bin membership is decided by exact fp32
  * sign tests against host-built boundary vectors.  Several points in one pixel: the
- * smallest range wins, ties to the lower point index; every point still records its
- * pixel.  Requires rows >= 2 and cols*az_step = 2*pi (full revolution; |error| < 1e-6).
- * Uses a handle-owned scratch of rows*cols 64-bit keys.
+ * pixel takes the smallest of their ranges; every point still records its pixel.
+ * Requires rows >= 2 and cols*az_step = 2*pi (full revolution; |error| < 1e-6).
+ * Uses a handle-owned scratch of rows*cols 32-bit keys.
  * Errors: FLIC_ERR_INVALID, FLIC_ERR_UNSUPPORTED (partial revolution), FLIC_ERR_OOM,
  * FLIC_ERR_CUDA.
  */
@@ -197,6 +197,29 @@ float* flic_range_buffer(flic_handle h);
  */
 flic_status flic_scatter(flic_handle h, const int32_t* labels, const int32_t* point_pixel,
                          int64_t n, int32_t* point_labels, void* stream);
+
+/*
+ * flic_project_batch — flic_project on nclouds clouds at once (no counterpart in the paper):
+ * three launches in all (keys cleared, points projected, range images decoded, at most 96
+ * clouds per launch), each cloud on its own handle's tables and key scratch, so the
+ * handles must be distinct.  Results equal flic_project cloud by cloud.
+ *   hs           host array of nclouds distinct handles (each able to project)
+ *   xyz          host array of nclouds device pointers (cloud i: n[i]*3 fp32)
+ *   n            host array of nclouds point counts (0 <= n[i] < 2^31)
+ *   range_out    host array of nclouds device pointers (rows_i*cols_i fp32), or NULL: the
+ *                handles' own buffers (flic_range_buffer)
+ *   point_pixel  host array of nclouds device pointers (n[i] int32)
+ * flic_scatter_batch — flic_scatter on nclouds clouds in one launch per 96 clouds:
+ *   labels[i] (rows_i*cols_i int32), point_pixel[i] and point_labels[i] (n[i] int32).
+ * The host arrays are read during the call only.  Errors: FLIC_ERR_INVALID (NULL, bad
+ * count, a handle repeated), FLIC_ERR_UNSUPPORTED (a handle cannot project), FLIC_ERR_CUDA.
+ */
+flic_status flic_project_batch(const flic_handle* hs, int32_t nclouds, const float* const* xyz,
+                               const int64_t* n, float* const* range_out,
+                               int32_t* const* point_pixel, void* stream);
+flic_status flic_scatter_batch(const flic_handle* hs, int32_t nclouds, const int32_t* const* labels,
+                               const int32_t* const* point_pixel, const int64_t* n,
+                               int32_t* const* point_labels, void* stream);
 
 /*
  * Batched labelling (no counterpart in the paper, which labels one frame at a time on one
@@ -432,10 +455,10 @@ double flic_server_clock(void);
  * (the paper has no counterpart; this is an integration entry point).  Some callers may
  * only use the buffers they are handed: code running inside a host framework whose
  * device memory belongs to its own pool, or plugins that must not call cudaMalloc.  This
- * call needs no handle and allocates nothing: its working memory (the 64-bit per-pixel
- * keys, the boundary tables and a status word) lives in static device arrays of fixed size
- * inside libflic, held by every GPU that loads the library until the process exits (about
- * 2.1 MiB).
+ * call needs no handle and allocates nothing: its working memory (the 32-bit per-pixel
+ * keys, the boundary and seed tables and a status word) lives in static device arrays of
+ * fixed size inside libflic, held by every GPU that loads the library until the process
+ * exits (about 1.1 MiB).
  *   rows, cols   2 <= rows <= FLIC_MAX_ROWS, cols <= FLIC_NOALLOC_MAX_COLS,
  *                rows*cols <= FLIC_NOALLOC_MAX_PIXELS; larger shapes give FLIC_ERR_INVALID
  *   elevation    host, rows doubles (radians, any order, distinct); az_step as in

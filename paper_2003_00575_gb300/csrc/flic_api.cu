@@ -144,8 +144,10 @@ struct flic_ctx {
     float* d_colb = nullptr;
     float* d_rowb = nullptr;
     int32_t* d_srow = nullptr;
+    flic::RowSeed* d_rseed = nullptr;
+    float rs_t0 = 0.0f, rs_inv_dt = 0.0f, col_margin = 0.5f;
     float inv_az_step = 0.0f;
-    unsigned long long* d_keys = nullptr;
+    uint32_t* d_keys = nullptr;
     int32_t* d_rl = nullptr;  // flic_filter_relabel scratch (relabel_scratch_ints)
     float* d_gnd = nullptr;   // ground table (flic_set_ground), nullptr: off
     float gnd_tan = 0.0f, gnd_height = 0.0f;
@@ -282,12 +284,16 @@ std::vector<float> build_kd_table(int R, const double* elev, double az_step, int
 
 // Projection boundaries (flic::build_proj_tables_into) in vectors of the right size.
 bool build_proj_tables(int R, int C, const double* elev, double az_step, std::vector<float>& colb,
-                       std::vector<float>& rowb, std::vector<int32_t>& srow) {
+                       std::vector<float>& rowb, std::vector<int32_t>& srow,
+                       std::vector<flic::RowSeed>& rseed, float* t0, float* inv_dt,
+                       float* col_margin) {
     if (R < 2) return false;
     colb.resize((size_t)2 * C);
     rowb.resize((size_t)2 * (R + 1));
     srow.resize(R);
-    return flic::build_proj_tables_into(R, C, elev, az_step, colb.data(), rowb.data(), srow.data());
+    rseed.resize(flic::kRowSeeds);
+    return flic::build_proj_tables_into(R, C, elev, az_step, colb.data(), rowb.data(), srow.data(),
+                                        rseed.data(), t0, inv_dt, col_margin);
 }
 
 template <typename T>
@@ -309,6 +315,7 @@ void free_ctx(flic_ctx* h) {
     cudaFree(h->d_colb);
     cudaFree(h->d_rowb);
     cudaFree(h->d_srow);
+    cudaFree(h->d_rseed);
     cudaFree(h->d_keys);
     cudaFree(h->d_rl);
     cudaFree(h->d_gnd);
@@ -395,16 +402,19 @@ flic_status flic_create_ex(int32_t rows, int32_t cols, const double* elevation, 
 
     std::vector<float> colb, rowb;
     std::vector<int32_t> srow;
+    std::vector<flic::RowSeed> rseed;
     bool full_turn = std::fabs((double)cols * az_step - kTwoPi) < 1e-6;
-    if (full_turn && build_proj_tables(rows, cols, elevation, az_step, colb, rowb, srow)) {
+    if (full_turn && build_proj_tables(rows, cols, elevation, az_step, colb, rowb, srow, rseed,
+                                       &h->rs_t0, &h->rs_inv_dt, &h->col_margin)) {
         if ((st = upload(&h->d_colb, colb, "column boundaries")) != FLIC_OK ||
             (st = upload(&h->d_rowb, rowb, "row boundaries")) != FLIC_OK ||
-            (st = upload(&h->d_srow, srow, "row order")) != FLIC_OK) {
+            (st = upload(&h->d_srow, srow, "row order")) != FLIC_OK ||
+            (st = upload(&h->d_rseed, rseed, "row seeds")) != FLIC_OK) {
             free_ctx(h);
             return st;
         }
         size_t npix = (size_t)rows * cols;
-        if ((e = cudaMalloc((void**)&h->d_keys, npix * sizeof(unsigned long long))) != cudaSuccess ||
+        if ((e = cudaMalloc((void**)&h->d_keys, npix * sizeof(uint32_t))) != cudaSuccess ||
             (e = cudaMalloc((void**)&h->d_range, npix * sizeof(float))) != cudaSuccess) {
             free_ctx(h);
             return cuda_fail(e, "projection buffers");
@@ -504,6 +514,10 @@ flic_status flic_project(flic_handle h, const float* xyz, int64_t n, float* rang
     P.colb = h->d_colb;
     P.rowb = h->d_rowb;
     P.srow = h->d_srow;
+    P.rseed = h->d_rseed;
+    P.rs_t0 = h->rs_t0;
+    P.rs_inv_dt = h->rs_inv_dt;
+    P.col_margin = h->col_margin;
     P.rows = h->R;
     P.cols = h->C;
     P.inv_az_step = h->inv_az_step;
@@ -517,6 +531,71 @@ flic_status flic_project(flic_handle h, const float* xyz, int64_t n, float* rang
 }
 
 float* flic_range_buffer(flic_handle h) { return h ? h->d_range : nullptr; }
+
+// The clouds' items, in launches of at most kProjBatchItems (a handle's key scratch serves
+// one cloud, so a repeated handle is refused).
+static flic_status proj_batches(const flic_handle* hs, int32_t nclouds, const float* const* xyz,
+                                const int64_t* n, float* const* range_out,
+                                int32_t* const* point_pixel, const int32_t* const* labels,
+                                int32_t* const* point_labels, std::vector<flic::ProjBatch>& out) {
+    if (nclouds < 0) return fail(FLIC_ERR_INVALID, "nclouds < 0");
+    if (nclouds > 0 && (!hs || !n || !point_pixel)) return fail(FLIC_ERR_INVALID, "NULL argument");
+    std::vector<const flic_ctx*> seen(hs, hs + nclouds);
+    std::sort(seen.begin(), seen.end());
+    if (std::adjacent_find(seen.begin(), seen.end()) != seen.end())
+        return fail(FLIC_ERR_INVALID, "a handle appears twice (each cloud needs its own scratch)");
+    out.clear();
+    for (int i = 0; i < nclouds; ++i) {
+        if (!hs[i]) return fail(FLIC_ERR_INVALID, "cloud %d: NULL handle", i);
+        if (n[i] > 0 && (!point_pixel[i] || (xyz && !xyz[i]) || (labels && !labels[i]) ||
+                         (point_labels && !point_labels[i])))
+            return fail(FLIC_ERR_INVALID, "cloud %d: NULL buffer", i);
+        if (out.empty() || out.back().nitems == flic::kProjBatchItems) {
+            out.emplace_back();
+            out.back().nitems = out.back().max_n = out.back().max_px = 0;
+        }
+        flic::ProjBatch& b = out.back();
+        flic::ProjItem& it = b.item[b.nitems];
+        flic_status st = flic::proj_item(hs[i], xyz ? xyz[i] : nullptr, n[i],
+                                         range_out ? range_out[i] : nullptr, point_pixel[i],
+                                         labels ? labels[i] : nullptr,
+                                         point_labels ? point_labels[i] : nullptr, &it);
+        if (st != FLIC_OK) return st;
+        ++b.nitems;
+        b.max_n = std::max(b.max_n, it.n);
+        b.max_px = std::max(b.max_px, hs[i]->R * hs[i]->C);
+    }
+    return FLIC_OK;
+}
+
+flic_status flic_project_batch(const flic_handle* hs, int32_t nclouds, const float* const* xyz,
+                               const int64_t* n, float* const* range_out,
+                               int32_t* const* point_pixel, void* stream) {
+    if (nclouds > 0 && !xyz) return fail(FLIC_ERR_INVALID, "NULL argument");
+    std::vector<flic::ProjBatch> pb;
+    flic_status st = proj_batches(hs, nclouds, xyz, n, range_out, point_pixel, nullptr, nullptr, pb);
+    if (st != FLIC_OK) return st;
+    for (const flic::ProjBatch& b : pb) {
+        cudaError_t e = flic::launch_project_batch(b, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "flic_project_batch launch");
+    }
+    return FLIC_OK;
+}
+
+flic_status flic_scatter_batch(const flic_handle* hs, int32_t nclouds, const int32_t* const* labels,
+                               const int32_t* const* point_pixel, const int64_t* n,
+                               int32_t* const* point_labels, void* stream) {
+    if (nclouds > 0 && (!labels || !point_labels)) return fail(FLIC_ERR_INVALID, "NULL argument");
+    std::vector<flic::ProjBatch> pb;
+    flic_status st = proj_batches(hs, nclouds, nullptr, n, nullptr,
+                                  const_cast<int32_t* const*>(point_pixel), labels, point_labels, pb);
+    if (st != FLIC_OK) return st;
+    for (const flic::ProjBatch& b : pb) {
+        cudaError_t e = flic::launch_scatter_batch(b, (cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(e, "flic_scatter_batch launch");
+    }
+    return FLIC_OK;
+}
 
 flic_status flic_scatter(flic_handle h, const int32_t* labels, const int32_t* point_pixel,
                          int64_t n, int32_t* point_labels, void* stream) {
@@ -1203,6 +1282,10 @@ flic_status flic::proj_item(flic_handle h, const float* xyz, int64_t n, float* r
     it.P.colb = h->d_colb;
     it.P.rowb = h->d_rowb;
     it.P.srow = h->d_srow;
+    it.P.rseed = h->d_rseed;
+    it.P.rs_t0 = h->rs_t0;
+    it.P.rs_inv_dt = h->rs_inv_dt;
+    it.P.col_margin = h->col_margin;
     it.P.rows = h->R;
     it.P.cols = h->C;
     it.P.inv_az_step = h->inv_az_step;

@@ -2,11 +2,15 @@
 // Not part of the public ABI (include/flic.h is).
 #pragma once
 
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdint>
+#include <limits>
 
 #include <cuda_runtime.h>
+
+#include "flic.h"
 
 namespace flic {
 
@@ -129,12 +133,24 @@ cudaError_t label_blocks_per_sm(int threads, size_t smem, int* out);
 cudaError_t launch_edges(const FrameDesc& f, uint16_t* mask, cudaStream_t stream);
 cudaError_t label_kernel_setup(size_t max_smem);
 
+constexpr int kRowSeeds = 2048;       // buckets of the row-band seed table
+constexpr uint32_t kRowOutside = 1023;  // a seed's row field: outside the field of view
+// One bucket of the row seed table: t = tan(elevation) of a point below tlo gives row A,
+// above thi row B, anything between is settled by the sign tests from band `band`.
+struct RowSeed {
+    uint32_t info;  // band (bits 0-9) | row A (bits 10-19) | row B (bits 20-29)
+    float tlo, thi;
+    uint32_t pad;
+};
 struct ProjDesc {
     const float* colb;      // cols x (cos, sin) of the column boundaries
     const float* rowb;      // (rows+1) x (cos, sin) of the sorted elevation boundaries
     const int32_t* srow;    // rows: row index of the j-th lowest beam
+    const RowSeed* rseed;   // kRowSeeds buckets of tan(elevation) between the outer bounds
+    float rs_t0, rs_inv_dt; // bucket = (z/rho - rs_t0) * rs_inv_dt; rs_inv_dt 0: no table
     int32_t rows, cols;
     float inv_az_step;      // 1 / az_step, only to seed the column search
+    float col_margin;       // a seed's column fraction in (margin, 1 - margin): column holds
     int32_t* status;
 };
 // The projection's boundary tables, written into caller-supplied arrays (no allocation):
@@ -143,9 +159,26 @@ struct ProjDesc {
 // and bounded by the midpoints of adjacent sorted elevations, the outer bands half a spacing
 // beyond their beam (rowb: (rows + 1) x (cos, sin)).  False when rows < 2 or two elevations
 // are equal.  flic_create and flic_project_noalloc both build their tables here.
+//
+// Seeds of the two searches, built so that where they skip the sign tests the tests' answer
+// is known.  Both rest on one bound: a boundary more than 1e-6 rad from a point gets the
+// sign of the exact test from its fp32 test (whose rounding error is below 4e-7 r).
+// - rseed (kRowSeeds buckets of t = tan(elevation) between the outer boundaries): the
+//   kernel's bucket of a point (t = z * rsqrt(rho^2), within 2.4e-7 |t| of z / rho) is
+//   within one of the point's own, so the point lies in the window of buckets b-1 .. b+1.
+//   No boundary within that window (widened by a 1e-6 rad margin): rows A = B = the
+//   window's row, limits +inf.  Exactly one boundary k: row A below it (band k-1), row B
+//   above (band k), kRowOutside past an outer boundary, and limits T_k -+ m with
+//   m = 2e-6 (1 + T_k^2) + 4e-7 (1 + |T_k|), T_k = tan(boundary k), rounded outward: a t
+//   outside [tlo, thi] is more than 1e-6 rad from boundary k on the same side.  Two or
+//   more: limits -inf, +inf (always settled).  *inv_dt = 0 (no table: a bisection) when an
+//   outer boundary lies beyond +-80 degrees.
+// - *col_margin: a column seed within 2e-6 rad of the azimuth (the kernel's polynomial is
+//   within 1.1e-6) whose column fraction lies in (margin, 1 - margin) keeps both column
+//   boundaries more than 1e-6 rad away, counting the fp32 rounding of seed * cols / 2pi.
 inline bool build_proj_tables_into(int R, int C, const double* elev, double az_step, float* colb,
-                                   float* rowb, int32_t* srow) {
-    if (R < 2) return false;
+                                   float* rowb, int32_t* srow, RowSeed* rseed, float* t0,
+                                   float* inv_dt, float* col_margin) {    if (R < 2) return false;
     for (int c = 0; c < C; ++c) {
         const double ang = (double)c * az_step;
         colb[2 * (size_t)c] = (float)std::cos(ang);
@@ -177,12 +210,60 @@ inline bool build_proj_tables_into(int R, int C, const double* elev, double az_s
         rowb[2 * (size_t)j] = (float)std::cos(m);
         rowb[2 * (size_t)j + 1] = (float)std::sin(m);
     }
+    const double kPi = 3.14159265358979323846;
+    *col_margin = (float)(2.0 * C * ((2.0e-6 + 1.0e-6) / (2.0 * kPi) + 1.2e-7));
+    if (*col_margin > 0.5f) *col_margin = 0.5f;  // nothing is certain: always settle
+    auto bound = [&](int j) {  // boundary j in double, as above
+        if (j == 0) return elev[srow[0]] - (elev[srow[1]] - elev[srow[0]]) / 2.0;
+        if (j == R) return elev[srow[R - 1]] + (elev[srow[R - 1]] - elev[srow[R - 2]]) / 2.0;
+        return (elev[srow[j - 1]] + elev[srow[j]]) / 2.0;
+    };
+    const double lim = 80.0 * kPi / 180.0;
+    const double m0 = bound(0), mR = bound(R);
+    *t0 = 0.0f;
+    *inv_dt = 0.0f;
+    const float inf = std::numeric_limits<float>::infinity();
+    for (int b = 0; b < kRowSeeds; ++b) rseed[b] = RowSeed{0u, -inf, inf, 0u};
+    if (m0 > -lim && mR < lim && R <= FLIC_MAX_ROWS) {
+        double tb[FLIC_MAX_ROWS + 1];  // tan of every boundary, ascending
+        for (int j = 0; j <= R; ++j) tb[j] = std::tan(bound(j));
+        const double ta = tb[0];
+        const double dt = (tb[R] - ta) / kRowSeeds;
+        auto row_of = [&](int band) {
+            return band < 0 || band >= R ? kRowOutside : (uint32_t)srow[band];
+        };
+        int j = 0;  // band at the bucket's lower edge
+        int k = 0;  // first boundary at or above the window's lower end
+        for (int b = 0; b < kRowSeeds; ++b) {
+            const double edge = ta + b * dt;
+            while (j + 1 < R && tb[j + 1] <= edge) ++j;
+            const double wlo = ta + (b - 1) * dt, whi = ta + (b + 2) * dt;
+            const double mg = 1.0e-6 * (1.0 + std::max(wlo * wlo, whi * whi));  // 1e-6 rad
+            while (k <= R && tb[k] < wlo - mg) ++k;
+            int inside = 0;
+            while (k + inside <= R && tb[k + inside] <= whi + mg) ++inside;
+            RowSeed& e = rseed[b];
+            e.info = (uint32_t)j;
+            if (inside == 0) {  // the window lies within band j
+                e.info |= row_of(j) << 10 | row_of(j) << 20;
+                e.tlo = e.thi = inf;
+            } else if (inside == 1) {
+                const double T = tb[k];
+                const double m = 2.0e-6 * (1.0 + T * T) + 4.0e-7 * (1.0 + std::fabs(T));
+                e.info |= row_of(k - 1) << 10 | row_of(k) << 20;
+                e.tlo = std::nextafter((float)(T - m), -inf);
+                e.thi = std::nextafter((float)(T + m), inf);
+            }  // else: settled, as initialised
+        }
+        *t0 = (float)ta;
+        *inv_dt = (float)(1.0 / dt);
+    }
     return true;
 }
 
 cudaError_t launch_project(const ProjDesc& P, const float* xyz, int64_t n,
-                           unsigned long long* keys, int32_t* point_pixel, cudaStream_t stream);
-cudaError_t launch_decode(const ProjDesc& P, const unsigned long long* keys, float* range_out,
+                           uint32_t* keys, int32_t* point_pixel, cudaStream_t stream);
+cudaError_t launch_decode(const ProjDesc& P, const uint32_t* keys, float* range_out,
                           cudaStream_t stream);
 
 // Many clouds projected (and later scattered) by one launch per kernel: every item is one
@@ -191,7 +272,7 @@ struct ProjItem {
     ProjDesc P;                   // the handle's tables, shape and status word
     const float* xyz;             // n x 3
     int32_t* point_pixel;         // n
-    unsigned long long* keys;     // rows x cols, the handle's scratch
+    uint32_t* keys;               // rows x cols, the handle's scratch
     float* range_out;             // rows x cols
     const int32_t* labels;        // rows x cols (scatter)
     int32_t* point_labels;        // n (scatter)
@@ -212,7 +293,6 @@ cudaError_t launch_scatter_batch(const ProjBatch& B, cudaStream_t stream);
 void set_last_error(const char* msg);
 
 }  // namespace flic
-#include "flic.h"
 namespace flic {
 // A new handle with the same geometry, threshold, skip, flags and tuning as h.
 flic_status clone_handle(flic_handle h, flic_handle* out, int* rows, int* cols);

@@ -47,6 +47,7 @@
 // cannot deadlock; the wait is bounded all the same and reports exhaustion in the
 // frame's status word, as does every union and find loop.  The last block to leave resets the queue's counters for the next
 // launch.  The labels buffer is the only global working memory besides those counters.
+#include <algorithm>
 #include <cstdint>
 
 #include "flic_device.cuh"
@@ -1129,6 +1130,126 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
     }
 }
 
+// flic_edges over 16-byte words: a thread owns one float4 (four adjacent columns) of
+// kEdgeRows consecutive rows.  All of its loads come first: the kEdgeRows + S words of its
+// column and the one or two words to the right of each of its rows (wrapped modulo the
+// row, or past its end without wrap).  A reading that is no measurement, and every word
+// beyond the frame, is held as +inf, which fails every test by itself: (a - inf)^2 and
+// K (a inf) are +inf or NaN.  So the tests need no validity or bounds checks, and run as
+// packed f32x2 pairs of adjacent pixels, each element the scalar sequence of edge_pred.
+// The four masks of a row leave as one 8-byte store.  Needs cols % 4 == 0, a 16-byte
+// aligned range image, an 8-byte aligned mask and no ground filter; other frames take the
+// one-pixel-per-thread kernel below.
+constexpr int kEdgeRows = 2;
+
+// (+inf, the one non-measurement that passes x > 0, is already the sentinel)
+__device__ __forceinline__ float inf_clean(float x) {
+    return x > 0.0f ? x : __int_as_float(0x7f800000);
+}
+
+// bit when d <= D2, else 0 (one set and one logic instruction)
+__device__ __forceinline__ unsigned bit_le(float d, float D2, unsigned bit) {
+    unsigned m;
+    asm("set.le.u32.f32 %0, %1, %2;" : "=r"(m) : "f"(d), "f"(D2));
+    return m & bit;
+}
+
+__device__ __forceinline__ float4 inf_clean4(float4 v) {
+    return make_float4(inf_clean(v.x), inf_clean(v.y), inf_clean(v.z), inf_clean(v.w));
+}
+
+__device__ __forceinline__ float4 inf4() {
+    const float i = __int_as_float(0x7f800000);
+    return make_float4(i, i, i, i);
+}
+
+// d2 of the pairs (a0, b0) and (a1, b1), both with the constant K.
+__device__ __forceinline__ void edge_d2_x2(float a0, float a1, float b0, float b1, float K,
+                                           float& d0, float& d1) {
+    unsigned long long A, B, KK, t, tt, ab, kab, d2;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(A) : "f"(a0), "f"(a1));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(B) : "f"(b0), "f"(b1));
+    asm("mov.b64 %0, {%1, %1};" : "=l"(KK) : "f"(K));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(t) : "l"(A), "l"(B));
+    asm("mul.rn.f32x2 %0, %1, %1;" : "=l"(tt) : "l"(t));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(ab) : "l"(A), "l"(B));
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(kab) : "l"(KK), "l"(ab));
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d2) : "l"(tt), "l"(kab));
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(d0), "=f"(d1) : "l"(d2));
+}
+
+template <int S>
+__global__ void __launch_bounds__(128) flic_edges_vec_kernel(const FrameDesc f,
+                                                             uint16_t* __restrict__ mask) {
+    const int Q = f.cols >> 2;  // words per row
+    const int RT = (f.rows + kEdgeRows - 1) / kEdgeRows;
+    const float4* __restrict__ rg = reinterpret_cast<const float4*>(f.range);
+    const int total = Q * RT;
+    const float D2 = f.delta2;
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const int rt = t / Q;
+        const int q = t - rt * Q;
+        const int r0 = rt * kEdgeRows;
+        const int c0 = q << 2;
+        int q1 = q + 1, q2 = q + 2;  // the words holding columns c0+4.. and c0+8..
+        const bool in1 = f.wrap || q1 < Q, in2 = f.wrap || q2 < Q;
+        while (q1 >= Q) q1 -= Q;
+        while (q2 >= Q) q2 -= Q;
+        float4 w[kEdgeRows + S], h1[kEdgeRows], h2[kEdgeRows];
+#pragma unroll
+        for (int i = 0; i < kEdgeRows + S; ++i)
+            w[i] = r0 + i < f.rows ? inf_clean4(__ldg(rg + (size_t)(r0 + i) * Q + q)) : inf4();
+#pragma unroll
+        for (int i = 0; i < kEdgeRows; ++i) {
+            const bool row = r0 + i < f.rows;
+            h1[i] = row && in1 ? inf_clean4(__ldg(rg + (size_t)(r0 + i) * Q + q1)) : inf4();
+            h2[i] = S >= 5 && row && in2 ? inf_clean4(__ldg(rg + (size_t)(r0 + i) * Q + q2))
+                                         : inf4();
+        }
+#pragma unroll
+        for (int i = 0; i < kEdgeRows; ++i) {
+            const int r = r0 + i;
+            if (r >= f.rows) break;
+            // row r, columns c0 .. c0 + 11
+            const float hv[12] = {w[i].x,  w[i].y,  w[i].z,  w[i].w,  h1[i].x, h1[i].y,
+                                  h1[i].z, h1[i].w, h2[i].x, h2[i].y, h2[i].z, h2[i].w};
+            unsigned m0 = 0u, m1 = 0u, m2 = 0u, m3 = 0u;
+#pragma unroll
+            for (int k = 1; k <= S; ++k) {
+                const float Kh = __ldg(f.kh + r * S + k - 1);
+                const float Kv = r + k < f.rows ? __ldg(f.kv + r * S + k - 1) : 0.0f;
+                const unsigned bh = 1u << (k - 1), bv = 1u << (8 + k - 1);
+                float d0, d1, d2, d3;
+                edge_d2_x2(hv[0], hv[1], hv[k], hv[k + 1], Kh, d0, d1);
+                edge_d2_x2(hv[2], hv[3], hv[k + 2], hv[k + 3], Kh, d2, d3);
+                m0 |= bit_le(d0, D2, bh);
+                m1 |= bit_le(d1, D2, bh);
+                m2 |= bit_le(d2, D2, bh);
+                m3 |= bit_le(d3, D2, bh);
+                const float4& v = w[i + k];
+                edge_d2_x2(hv[0], hv[1], v.x, v.y, Kv, d0, d1);
+                edge_d2_x2(hv[2], hv[3], v.z, v.w, Kv, d2, d3);
+                m0 |= bit_le(d0, D2, bv);
+                m1 |= bit_le(d1, D2, bv);
+                m2 |= bit_le(d2, D2, bv);
+                m3 |= bit_le(d3, D2, bv);
+            }
+            if (S > 1 && f.lattice) {  // sparse Map Connection: offset 1 everywhere, offset S
+                const unsigned far = (1u << (S - 1)) | (1u << (8 + S - 1));  // from lattice
+                const bool rok = r % S == 0;                                 // points only
+                m0 &= 0x0101u | (rok && (c0 + 0) % S == 0 ? far : 0u);
+                m1 &= 0x0101u | (rok && (c0 + 1) % S == 0 ? far : 0u);
+                m2 &= 0x0101u | (rok && (c0 + 2) % S == 0 ? far : 0u);
+                m3 &= 0x0101u | (rok && (c0 + 3) % S == 0 ? far : 0u);
+            }
+            uint2 out;
+            out.x = m0 | (m1 << 16);
+            out.y = m2 | (m3 << 16);
+            *reinterpret_cast<uint2*>(mask + (size_t)r * f.cols + c0) = out;
+        }
+    }
+}
+
 // flic_edges: the neighbour test alone, one pixel per thread, straight from global memory.
 __global__ void flic_edges_kernel(const FrameDesc f, uint16_t* __restrict__ mask) {
     const int N = f.rows * f.cols;
@@ -1180,9 +1301,50 @@ cudaError_t label_blocks_per_sm(int threads, size_t smem, int* out) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, flic_label_kernel, threads, smem);
 }
 
+// One resident wave of 128-thread blocks (grid-stride over the tiles): no second partial
+// wave and no ramp between waves.
+template <int S>
+static cudaError_t launch_edges_vec(const FrameDesc& f, uint16_t* mask, int work,
+                                    cudaStream_t stream) {
+    static int per_sm[64];  // resident blocks per SM, by device (0: not yet known)
+    static int sms[64];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) dev = 63;
+    if (per_sm[dev] <= 0) {
+        int b = 0, n = 0;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, flic_edges_vec_kernel<S>, 128,
+                                                               0)) != cudaSuccess ||
+            (e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+            return e;
+        sms[dev] = n > 0 ? n : 1;
+        per_sm[dev] = b > 0 ? b : 1;
+    }
+    int blocks = (work + 127) / 128;
+    blocks = std::max(1, std::min(blocks, per_sm[dev] * sms[dev]));
+    flic_edges_vec_kernel<S><<<blocks, 128, 0, stream>>>(f, mask);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_edges(const FrameDesc& f, uint16_t* mask, cudaStream_t stream) {
     const int N = f.rows * f.cols;
     const int threads = 256;
+    const bool vec = f.cols % 4 == 0 && !f.gnd && f.skip >= 1 && f.skip <= 8 &&
+                     ((uintptr_t)f.range & 15) == 0 && ((uintptr_t)mask & 7) == 0;
+    if (vec) {
+        const int work = (f.cols / 4) * ((f.rows + kEdgeRows - 1) / kEdgeRows);
+        switch (f.skip) {
+            case 1: return launch_edges_vec<1>(f, mask, work, stream);
+            case 2: return launch_edges_vec<2>(f, mask, work, stream);
+            case 3: return launch_edges_vec<3>(f, mask, work, stream);
+            case 4: return launch_edges_vec<4>(f, mask, work, stream);
+            case 5: return launch_edges_vec<5>(f, mask, work, stream);
+            case 6: return launch_edges_vec<6>(f, mask, work, stream);
+            case 7: return launch_edges_vec<7>(f, mask, work, stream);
+            default: return launch_edges_vec<8>(f, mask, work, stream);
+        }
+    }
     int blocks = (N + threads - 1) / threads;
     if (blocks < 1) blocks = 1;
     flic_edges_kernel<<<blocks, threads, 0, stream>>>(f, mask);

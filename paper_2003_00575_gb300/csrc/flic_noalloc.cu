@@ -39,20 +39,22 @@ constexpr int kNoAllocMaxRows = FLIC_MAX_ROWS;
 constexpr int kMaxDevices = 64;
 
 // the working memory: file-scope static device arrays (see the comment above)
-static __device__ __align__(256) unsigned long long g_keys[kNoAllocMaxPixels];
+static __device__ __align__(256) uint32_t g_keys[kNoAllocMaxPixels];
 static __device__ __align__(256) float g_colb[2 * kNoAllocMaxCols];
 static __device__ __align__(256) float g_rowb[2 * (kNoAllocMaxRows + 1)];
 static __device__ __align__(256) int32_t g_srow[kNoAllocMaxRows];
+static __device__ __align__(256) flic::RowSeed g_rseed[flic::kRowSeeds];
 static __device__ __align__(256) int32_t g_status;
 
 namespace {
 
 struct DevicePtrs {
     bool ready = false;
-    unsigned long long* keys = nullptr;
+    uint32_t* keys = nullptr;
     float* colb = nullptr;
     float* rowb = nullptr;
     int32_t* srow = nullptr;
+    flic::RowSeed* rseed = nullptr;
     int32_t* status = nullptr;
 };
 
@@ -62,6 +64,7 @@ DevicePtrs g_dev[kMaxDevices];
 float h_colb[2 * kNoAllocMaxCols];
 float h_rowb[2 * (kNoAllocMaxRows + 1)];
 int32_t h_srow[kNoAllocMaxRows];
+flic::RowSeed h_rseed[flic::kRowSeeds];
 
 flic_status na_fail(flic_status st, const char* fmt, ...) {
     char msg[256];
@@ -113,11 +116,14 @@ extern "C" flic_status flic_project_noalloc(int32_t rows, int32_t cols, const do
             (e = cudaGetSymbolAddress((void**)&d.colb, g_colb)) != cudaSuccess ||
             (e = cudaGetSymbolAddress((void**)&d.rowb, g_rowb)) != cudaSuccess ||
             (e = cudaGetSymbolAddress((void**)&d.srow, g_srow)) != cudaSuccess ||
+            (e = cudaGetSymbolAddress((void**)&d.rseed, g_rseed)) != cudaSuccess ||
             (e = cudaGetSymbolAddress((void**)&d.status, g_status)) != cudaSuccess)
             return cuda_err(e, "cudaGetSymbolAddress");
         d.ready = true;
     }
-    if (!flic::build_proj_tables_into(rows, cols, elevation, az_step, h_colb, h_rowb, h_srow))
+    float rs_t0 = 0.0f, rs_inv_dt = 0.0f, col_margin = 0.5f;
+    if (!flic::build_proj_tables_into(rows, cols, elevation, az_step, h_colb, h_rowb, h_srow,
+                                      h_rseed, &rs_t0, &rs_inv_dt, &col_margin))
         return na_fail(FLIC_ERR_UNSUPPORTED, "flic_project_noalloc: elevations must be distinct");
     // pageable host source: each copy returns once the host data has been staged
     if ((e = cudaMemcpyAsync(d.colb, h_colb, sizeof(float) * 2 * (size_t)cols,
@@ -126,12 +132,18 @@ extern "C" flic_status flic_project_noalloc(int32_t rows, int32_t cols, const do
                              cudaMemcpyHostToDevice, s)) != cudaSuccess ||
         (e = cudaMemcpyAsync(d.srow, h_srow, sizeof(int32_t) * (size_t)rows,
                              cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d.rseed, h_rseed, sizeof(h_rseed), cudaMemcpyHostToDevice, s)) !=
+            cudaSuccess ||
         (e = cudaMemsetAsync(d.status, 0, sizeof(int32_t), s)) != cudaSuccess)
         return cuda_err(e, "table upload");
     flic::ProjDesc P{};
     P.colb = d.colb;
     P.rowb = d.rowb;
     P.srow = d.srow;
+    P.rseed = d.rseed;
+    P.rs_t0 = rs_t0;
+    P.rs_inv_dt = rs_inv_dt;
+    P.col_margin = col_margin;
     P.rows = rows;
     P.cols = cols;
     P.inv_az_step = (float)(1.0 / az_step);

@@ -49,6 +49,8 @@ SIGNATURES = {
     "flic_destroy": (_I32, [_P]),
     "flic_get_tables": (_I32, [_P, _P, _P]),
     "flic_get_diag_table": (_I32, [_P, _P]),
+    "flic_project_batch": (_I32, [_P, _I32, _P, _P, _P, _P, _P]),
+    "flic_scatter_batch": (_I32, [_P, _I32, _P, _P, _P, _P, _P]),
     "flic_edges": (_I32, [_P, _P, _P, _P]),
     "flic_label": (_I32, [_P, _P, _P, _P]),
     "flic_project": (_I32, [_P, _P, _I64, _P, _P, _P]),
@@ -230,6 +232,44 @@ def flic_project(h: Handle, xyz, range_out, point_pixel, stream=None) -> None:
     _check(_lib.flic_project(h.ptr, _dptr(xyz, "float32", None, "xyz"), n,
                              _dptr(range_out, "float32", h.npix, "range_out"),
                              _dptr(point_pixel, "int32", n, "point_pixel"), _stream(stream)))
+
+
+class CloudArgs:
+    """Host pointer arrays for flic_project_batch / flic_scatter_batch (one distinct handle
+    per cloud), built once and reusable across calls."""
+
+    def __init__(self, handles, xyz, point_pixel, range_out=None, labels=None,
+                 point_labels=None):
+        k = len(handles)
+        if len({h.ptr for h in handles}) != k:
+            raise ValueError("every cloud needs its own handle")
+        self.n = k
+        self.hs = (ctypes.c_void_p * k)(*[h.ptr for h in handles])
+        counts = [x.numel() // 3 for x in xyz]
+        self.counts = (ctypes.c_int64 * k)(*counts)
+        self.xyz = (ctypes.c_void_p * k)(*[_dptr(x, "float32", 3 * c, "xyz")
+                                           for x, c in zip(xyz, counts)])
+        self.pix = (ctypes.c_void_p * k)(*[_dptr(p, "int32", c, "point_pixel")
+                                           for p, c in zip(point_pixel, counts)])
+        self.rng = None if range_out is None else (ctypes.c_void_p * k)(
+            *[_dptr(r, "float32", h.npix, "range_out") for r, h in zip(range_out, handles)])
+        self.lab = None if labels is None else (ctypes.c_void_p * k)(
+            *[_dptr(l, "int32", h.npix, "labels") for l, h in zip(labels, handles)])
+        self.plab = None if point_labels is None else (ctypes.c_void_p * k)(
+            *[_dptr(p, "int32", c, "point_labels") for p, c in zip(point_labels, counts)])
+        self._keep = (handles, xyz, point_pixel, range_out, labels, point_labels)
+
+
+def flic_project_batch(args: CloudArgs, stream=None) -> None:
+    _check(_lib.flic_project_batch(args.hs, args.n, args.xyz, args.counts, args.rng, args.pix,
+                                   _stream(stream)))
+
+
+def flic_scatter_batch(args: CloudArgs, stream=None) -> None:
+    if args.lab is None or args.plab is None:
+        raise ValueError("flic_scatter_batch needs labels and point_labels")
+    _check(_lib.flic_scatter_batch(args.hs, args.n, args.lab, args.pix, args.counts, args.plab,
+                                   _stream(stream)))
 
 
 def flic_range_buffer(h: Handle) -> int:

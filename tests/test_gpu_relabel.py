@@ -154,3 +154,90 @@ def test_out_of_frame_labels_are_reported(flic):
         assert flic.flic_device_status(h) == flic.FLIC_OK  # cleared
     finally:
         h.close()
+
+
+def _labelled(flic, frames):
+    hs = [flic.flic_create(f.sensor.rows, f.sensor.cols, f.sensor.elevation, f.sensor.az_step,
+                           f.delta, f.skip) for f in frames]
+    ls = []
+    for f, h in zip(frames, hs):
+        r = torch.from_numpy(f.range.reshape(-1)).to(DEV)
+        lab = torch.empty(f.range.size, dtype=torch.int32, device=DEV)
+        flic.flic_label(h, r, lab)
+        ls.append(lab)
+    torch.cuda.synchronize()
+    return hs, ls
+
+
+def _want(f, m):
+    ref = oracle.label(f.range, f.sensor.elevation, f.sensor.az_step, f.delta, f.skip)
+    return oracle.filter_relabel(ref, m)
+
+
+def test_batch_scratch_across_changing_frame_sets(flic):
+    """One batch object, consecutive calls on different frame sets (fewer tiles, then more,
+    which regrows the scratch, then fewer again): the counts left at the previous call's
+    roots are reset, every call equals the oracle."""
+    b = flic.flic_batch_create(64)
+    sets = [synth.config_c4(12, 300), synth.config_c4(3, 400), synth.config_c4(40, 500),
+            synth.config_c4(5, 600), synth.config_c4(12, 300)]
+    try:
+        for k, frames in enumerate(sets):
+            hs, ls = _labelled(flic, frames)
+            try:
+                num = torch.full((len(frames),), -7, dtype=torch.int32, device=DEV)
+                m = (100, 1, 30, 100, 7)[k]
+                flic.flic_filter_relabel_batch(b, _LabelArgs(flic, hs, ls), m, num)
+                torch.cuda.synchronize()
+                for i, f in enumerate(frames):
+                    want, n = _want(f, m)
+                    assert np.array_equal(ls[i].cpu().numpy(), want.reshape(-1)), (k, i)
+                    assert int(num[i].item()) == n, (k, i)
+                assert all(flic.flic_device_status(h) == flic.FLIC_OK for h in hs)
+            finally:
+                for h in hs:
+                    h.close()
+    finally:
+        b.close()
+
+
+class _LabelArgs:
+    """BatchArgs for flic_filter_relabel_batch, which reads only the handles and labels."""
+
+    def __init__(self, flic, hs, ls):
+        import ctypes
+        n = len(hs)
+        self.n = n
+        self.hs = (ctypes.c_void_p * n)(*[h.ptr for h in hs])
+        self.rs = None
+        self.ls = (ctypes.c_void_p * n)(*[x.data_ptr() for x in ls])
+        self._keep = (hs, ls)
+
+
+def test_single_handle_consecutive_calls_and_stray_labels(flic):
+    """One handle, one frame shape: different frames' labels one after another, and in
+    between a call on labels that point at pixels which are not roots (unspecified ids):
+    the calls after it are still exact."""
+    s = synth.c5_sensors()[2]
+    frames = [synth.c5_frame(s, 700 + i, as_cloud=False) for i in range(4)]
+    h = flic.flic_create(s.rows, s.cols, s.elevation, s.az_step, 0.5, 3)
+    try:
+        num = torch.full((1,), -7, dtype=torch.int32, device=DEV)
+        for k, f in enumerate(frames):
+            r = torch.from_numpy(f.range.reshape(-1)).to(DEV)
+            lab = torch.empty(f.range.size, dtype=torch.int32, device=DEV)
+            flic.flic_label(h, r, lab)
+            if k == 2:  # stray labels: every valid pixel points at its right-hand neighbour
+                stray = torch.where(lab >= 0, (torch.arange(lab.numel(), device=DEV) + 1)
+                                    % lab.numel(), lab).to(torch.int32)
+                flic.flic_filter_relabel(h, stray, 10, num)
+                torch.cuda.synchronize()
+            flic.flic_filter_relabel(h, lab, 10, num)
+            torch.cuda.synchronize()
+            want, n = oracle.filter_relabel(
+                oracle.label(f.range, s.elevation, s.az_step, 0.5, 3), 10)
+            assert np.array_equal(lab.cpu().numpy(), want.reshape(-1)), k
+            assert int(num.item()) == n, k
+        assert flic.flic_device_status(h) == flic.FLIC_OK
+    finally:
+        h.close()

@@ -276,19 +276,28 @@ def fp64_flip_count(oracle, synth, c4_frames):
     sets = {"c1": [synth.config_c1()], "c2": [synth.config_c2()],
             "c3": [synth.config_c3(with_xyz=False)], "c4": c4_frames}
     for name, fr in sets.items():
-        pairs = flips = 0
-        dev = 0.0
+        pairs = flips = lit_flips = lit_far = 0
+        dev = lit_dev = 0.0
         for f in fr:
             p, n, d = oracle.flips(f.range, f.sensor.elevation, f.sensor.az_step, f.delta, f.skip)
             pairs += p
             flips += n
             dev = max(dev, d)
+            _, n2, far2, d2 = oracle.flips_paper_form(f.range, f.sensor.elevation,
+                                                      f.sensor.az_step, f.delta, f.skip)
+            lit_flips += n2
+            lit_far += far2
+            lit_dev = max(lit_dev, d2)
         assert flips == 0 or dev < 1e-5, (name, flips, dev)
         out[name] = {"frames": len(fr), "pairs": pairs, "flips": flips,
-                     "max_abs_d_minus_delta_m": dev}
+                     "max_abs_d_minus_delta_m": dev,
+                     "literal_eq3_form": {"flips": lit_flips, "flips_beyond_bound": lit_far,
+                                          "max_abs_d_minus_delta_m": lit_dev}}
     out["bound_m"] = 1e-5
     out["note"] = ("oracle.flips in the CPU-baseline leg, outside the timed region; the GPU "
-                   "edge bits equal the oracle's bit for bit, so the counts hold for both")
+                   "edge bits equal the oracle's bit for bit, so the counts hold for both. "
+                   "literal_eq3_form: the same pairs decided by Eq. 3 as printed, "
+                   "d1*d1 + d2*d2 - (2 cos alpha)*d1*d2 in fp32 (a diagnostic; not used)")
     return out
 
 

@@ -78,6 +78,8 @@ def _load():
         lib.oracle_label.restype = i64
         lib.oracle_flips.argtypes = [i32, i32, P, P, f64, P, P, i32, f32, i32, P, P]
         lib.oracle_flips.restype = None
+        lib.oracle_flips_paper_form.argtypes = [i32, i32, P, P, f64, i32, f32, i32, P, P]
+        lib.oracle_flips_paper_form.restype = None
         lib.oracle_proj_tables.argtypes = [i32, i32, P, f64, P, P, P]
         lib.oracle_proj_tables.restype = i32
         lib.oracle_project.argtypes = [i32, i32, P, f64, P, i64, P, P, P]
@@ -192,6 +194,21 @@ def flips(range_img, elevation, az_step: float, delta: float, skip: int, wrap: b
     _load().oracle_flips(R, C, _ptr(rng), _ptr(elev), float(az_step), _ptr(kv), _ptr(kh), skip,
                          float(np.float32(delta)), int(bool(wrap)), _ptr(out), _ptr(dev))
     return int(out[0]), int(out[1]), float(dev[0])
+
+
+def flips_paper_form(range_img, elevation, az_step: float, delta: float, skip: int,
+                     wrap: bool = True):
+    """(candidate_pairs, flips, flips with |D - delta| >= 1e-5 m, max |D - delta|) of the
+    literal Eq. 3 form d1*d1 + d2*d2 - (2 cos alpha)*d1*d2 against the double-precision
+    Eq. 2, for one frame (a diagnostic of the cancellation the main form avoids)."""
+    rng = _f32(range_img)
+    R, C = rng.shape
+    out = np.zeros(3, np.int64)
+    dev = np.zeros(1, np.float64)
+    _load().oracle_flips_paper_form(R, C, _ptr(rng), _ptr(_f64(elevation)), float(az_step), skip,
+                                    float(np.float32(delta)), int(bool(wrap)), _ptr(out),
+                                    _ptr(dev))
+    return int(out[0]), int(out[1]), int(out[2]), float(dev[0])
 
 
 def proj_tables(rows: int, cols: int, elevation, az_step: float):

@@ -17,6 +17,8 @@
  *   oracle_label      connected-component labelling by breadth-first search, one
  *                     component at a time in raster order (§III-B-1), label = min index
  *   oracle_flips      FP64 decision of every candidate pair against the fp32 one
+ *   oracle_flips_paper_form
+ *                     the same for the literal form of Eq. 3 (a diagnostic)
  *   oracle_project    spherical projection of xyz points into the range image (§I)
  *   oracle_scatter    labels back onto the points (§I, Fig. 1)
  *   oracle_ground     ground extraction by the angle to the reading above (§III-A, Eq. 1
@@ -304,6 +306,61 @@ void oracle_flips(int32_t R, int32_t C, const float* range, const double* elev, 
     }
     out[0] = pairs;
     out[1] = flips;
+    max_dev[0] = worst;
+}
+
+/* The same candidate pairs decided by the literal form of Eq. 3 (oracle_pred_paper_form,
+ * C2 = (float)(2 cos alpha) from the double angle) against the double-precision Eq. 2:
+ * out = {pairs, flips, flips with |D - delta| >= 1e-5 m}, max_dev = the largest |D - delta|
+ * over the flips.  Diagnostic only: it shows what the cancellation-free form avoids. */
+void oracle_flips_paper_form(int32_t R, int32_t C, const float* range, const double* elev,
+                             double az_step, int32_t S, float delta, int32_t wrap, int64_t* out,
+                             double* max_dev) {
+    float delta2 = oracle_delta2(delta);
+    double d64 = (double)delta;
+    int64_t pairs = 0, flips = 0, far = 0;
+    double worst = 0.0;
+    for (int32_t r = 0; r < R; ++r) {
+        for (int32_t c = 0; c < C; ++c) {
+            float a = range[(int64_t)r * C + c];
+            if (!oracle_valid(a)) continue;
+            for (int32_t k = 1; k <= S; ++k) {
+                for (int vert = 0; vert <= 1; ++vert) {
+                    int32_t rr = r, cc = c;
+                    double alpha;
+                    if (vert) {
+                        rr = r + k;
+                        if (rr >= R) continue;
+                        alpha = fabs(elev[rr] - elev[r]);
+                    } else {
+                        cc = c + k;
+                        if (cc >= C) {
+                            if (!wrap) continue;
+                            cc = cc % C;
+                        }
+                        alpha = (double)k * az_step;
+                    }
+                    float b = range[(int64_t)rr * C + cc];
+                    if (!oracle_valid(b)) continue;
+                    ++pairs;
+                    int f32 = oracle_pred_paper_form(a, b, (float)(2.0 * cos(alpha)), delta2);
+                    double da = (double)a, db = (double)b;
+                    double sa = sin(alpha / 2.0);
+                    double D = sqrt((da - db) * (da - db) + 4.0 * da * db * sa * sa);
+                    int f64 = D <= d64 ? 1 : 0;
+                    if (f32 != f64) {
+                        ++flips;
+                        double dev = fabs(D - d64);
+                        if (dev >= 1e-5) ++far;
+                        if (dev > worst) worst = dev;
+                    }
+                }
+            }
+        }
+    }
+    out[0] = pairs;
+    out[1] = flips;
+    out[2] = far;
     max_dev[0] = worst;
 }
 

@@ -389,3 +389,43 @@ def test_fp64_flips_near_ties():
                 and abs(D - float(delta)) >= 1e-5:
             far += 1
     assert far > 0
+
+
+def test_frame_flips_of_the_literal_form():
+    """oracle.flips_paper_form counts the same candidate pairs as oracle.flips and decides
+    each by the scalar literal-form predicate (checked pair by pair on a small frame); on
+    c3 the literal form of Eq. 3 flips decisions further than 1e-5 m from delta, the
+    cancellation-free form none."""
+    g = np.random.default_rng(12)
+    R, C, S = 6, 40, 3
+    rng = (g.uniform(20.0, 90.0, (R, C))).astype(np.float32)
+    rng[g.random((R, C)) < 0.2] = 0.0
+    elev = np.radians(np.linspace(10.0, -10.0, R))
+    az = 2 * math.pi / C
+    delta = 2.5
+    pairs, flips, far, dev = oracle.flips_paper_form(rng, elev, az, delta, S)
+    want_pairs = want_flips = 0
+    for r in range(R):
+        for c in range(C):
+            a = rng[r, c]
+            if not a > 0:
+                continue
+            for k in range(1, S + 1):
+                for rr, cc, alpha in ((r + k, c, abs(elev[min(r + k, R - 1)] - elev[r])),
+                                      (r, (c + k) % C, k * az)):
+                    if rr >= R or not rng[rr, cc] > 0:
+                        continue
+                    b = rng[rr, cc]
+                    want_pairs += 1
+                    f32 = oracle.pred_paper_form(a, b, float(np.float32(2 * math.cos(alpha))),
+                                                 delta)
+                    D = math.sqrt((float(a) - float(b)) ** 2
+                                  + 4 * float(a) * float(b) * math.sin(alpha / 2) ** 2)
+                    want_flips += f32 != (D <= delta)
+    assert (pairs, flips) == (want_pairs, want_flips)
+    from paper_2003_00575_gb300 import synth
+    f = synth.config_c3(with_xyz=False)
+    p, n, d = oracle.flips(f.range, f.sensor.elevation, f.sensor.az_step, f.delta, f.skip)
+    p2, n2, far2, d2 = oracle.flips_paper_form(f.range, f.sensor.elevation, f.sensor.az_step,
+                                               f.delta, f.skip)
+    assert p == p2 and n == 0 and far2 > 0 and d2 >= 1e-5

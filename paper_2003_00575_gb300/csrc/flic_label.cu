@@ -270,30 +270,51 @@ __device__ void phase1_ground(const Strip& s, const Carve& sm) {
     __syncthreads();
 }
 
+// 0c. Every staged reading that is no measurement becomes +inf (after the ground pass,
+//     which clears ground readings to 0).  A pair with such a reading then fails the edge
+//     test by itself: (a - inf)^2 and K (a inf) are +inf or NaN, and so is d2.  The row
+//     pitch is a multiple of 4, so the pass runs over float4s (padding included, never
+//     read).
+__device__ __forceinline__ float no_reading() { return __int_as_float(0x7f800000); }
+
+__device__ __forceinline__ float clean_reading(float x) { return x > 0.0f ? x : no_reading(); }
+
+__device__ void phase1_clean(const Strip& s, const Carve& sm) {
+    float4* st = reinterpret_cast<float4*>(sm.stage);
+    const int n4 = (s.R * s.RP) >> 2;
+    for (int i = threadIdx.x; i < n4; i += blockDim.x) {
+        float4 v = st[i];
+        v.x = clean_reading(v.x);
+        v.y = clean_reading(v.y);
+        v.z = clean_reading(v.z);
+        v.w = clean_reading(v.w);
+        st[i] = v;
+    }
+    __syncthreads();
+}
+
 // The 2S + 1 ballot words of one 32-column chunk of row `row` (lanes = columns).  An
 // interior chunk has S rows below it and S columns right of it inside the strip, so it
 // needs no bounds tests.  Right edges whose far end lies past the strip are left out (the
-// boundary merge tests them).  With a valid, a neighbour b is a measurement iff b > 0:
-// +inf and NaN fail d2 <= delta2 by themselves.
+// boundary merge tests them).  The staged readings are clean (phase1_clean): a pixel is a
+// measurement iff its reading is below +inf, and a pair passes the test only if both are.
 template <int S, bool kInterior>
 __device__ __forceinline__ void mask_chunk(const Strip& s, const float* row, int c, int down,
                                            const float (&kh)[S], const float (&kv)[S],
                                            unsigned (&w)[2 * S + 1]) {
     const bool in = kInterior || c < s.W;
-    const float a = in ? row[c] : 0.0f;
-    const bool va = valid_range(a);
-    w[0] = __ballot_sync(kFull, va);
+    const float a = in ? row[c] : no_reading();
+    w[0] = __ballot_sync(kFull, a < no_reading());
 #pragma unroll
     for (int k = 1; k <= S; ++k) {
         const bool hin = kInterior || c + k < s.W;
         const bool vin = kInterior || (in && k <= down);
-        const float b = hin ? row[c + k] : 0.0f;
-        const float d = vin ? row[c + k * s.RP] : 0.0f;
+        const float b = hin ? row[c + k] : no_reading();
+        const float d = vin ? row[c + k * s.RP] : no_reading();
         float dh, dv;
         edge_d2_pair(a, b, d, kh[k - 1], kv[k - 1], dh, dv);
-        // the pixel's own validity is applied once per word
-        w[k] = __ballot_sync(kFull, (b > 0.0f) & (dh <= s.delta2)) & w[0];
-        w[S + k] = __ballot_sync(kFull, (d > 0.0f) & (dv <= s.delta2)) & w[0];
+        w[k] = __ballot_sync(kFull, dh <= s.delta2);
+        w[S + k] = __ballot_sync(kFull, dv <= s.delta2);
     }
 }
 
@@ -305,19 +326,19 @@ __device__ __forceinline__ void diag_chunk(const Strip& s, const float* row, int
                                            const float (&kd)[S], unsigned w0,
                                            unsigned (&d)[2 * S + 1]) {
     const bool in = kInterior || c < s.W;
-    const float a = in ? row[c] : 0.0f;
+    const float a = in ? row[c] : no_reading();
     d[0] = 0u;
 #pragma unroll
     for (int k = 1; k <= S; ++k) {
         const bool vin = kInterior || (in && k <= down);
         const bool rin = vin && (kInterior || c + k < s.W);
         const bool lin = vin && c >= k;
-        const float br = rin ? row[c + k + k * s.RP] : 0.0f;
-        const float bl = lin ? row[c - k + k * s.RP] : 0.0f;
+        const float br = rin ? row[c + k + k * s.RP] : no_reading();
+        const float bl = lin ? row[c - k + k * s.RP] : no_reading();
         float dr, dl;
         edge_d2_pair(a, br, bl, kd[k - 1], kd[k - 1], dr, dl);
-        d[k] = __ballot_sync(kFull, (br > 0.0f) & (dr <= s.delta2)) & w0;
-        d[S + k] = __ballot_sync(kFull, (bl > 0.0f) & (dl <= s.delta2)) & w0;
+        d[k] = __ballot_sync(kFull, dr <= s.delta2);
+        d[S + k] = __ballot_sync(kFull, dl <= s.delta2);
     }
 }
 
@@ -709,6 +730,7 @@ __device__ __noinline__ void phase1_diag(const Strip& s, const Carve& sm) {
 
 __device__ __forceinline__ void phase1(const Strip& s, const Carve& sm) {
     if (s.gnd) phase1_ground(s, sm);
+    phase1_clean(s, sm);
     if (s.kd) {  // with the diagonal Map Connections
         phase1_diag(s, sm);
         return;

@@ -158,11 +158,13 @@ __global__ void __launch_bounds__(kThreads) relabel_count(const RelabelLaunch L)
     const int p0 = (t - F.tile0) * kRelabelTile;
     int c = 0;
     if (threadIdx.x < kWords) {
-        unsigned r = __ldcg(L.roots + (size_t)t * kWords + threadIdx.x), k = 0;
-        while (r) {
-            const int b = __ffs(r) - 1;
-            r &= r - 1u;
-            if (__ldcg(F.cnt + p0 + 32 * threadIdx.x + b) >= L.min_size) k |= 1u << b;
+        const unsigned r = __ldcg(L.roots + (size_t)t * kWords + threadIdx.x);
+        unsigned k = 0;
+        if (r) {  // the counts of the word's roots, all loads in flight at once
+            const int32_t* wc = F.cnt + p0 + 32 * threadIdx.x;
+#pragma unroll
+            for (int b = 0; b < 32; ++b)
+                if (((r >> b) & 1u) && __ldcg(wc + b) >= L.min_size) k |= 1u << b;
         }
         __stcg(L.kept + (size_t)t * kWords + threadIdx.x, k);
         c = __popc(k);

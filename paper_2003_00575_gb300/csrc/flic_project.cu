@@ -120,14 +120,15 @@ __device__ __forceinline__ int settle_col(const ProjDesc& P, float x, float y, i
     return c;
 }
 
-// Pixels of N points of a cloud (indices i0 .. i0 + N - 1) on a handle with a seed table:
-// the arithmetic of all N first, then their N table loads at once, then the rare settles,
-// the pixels and the keys offered to them (the smallest range wins).  Every index computed from a point that is no measurement stays in bounds
-// (NaN converts to 0; the bucket and column are clamped) and is not used.
+// Pixels of N points of a cloud on a handle with a seed table: the arithmetic of all N
+// first, then their N table loads at once, then the rare settles, the pixels and the keys
+// offered to them (the smallest range wins).  Every index computed from a point that is no
+// measurement stays in bounds (NaN converts to 0; the bucket and column are clamped) and
+// is not used.
 template <int N>
 __device__ __forceinline__ void project_group(const ProjDesc& P, const RowSeed* seeds,
                                               const float (&x)[N], const float (&y)[N],
-                                              const float (&z)[N], uint32_t i0,
+                                              const float (&z)[N],
                                               uint32_t* __restrict__ keys,
                                               int32_t (&out)[N]) {
     float rg[N], rho2[N], fr[N], t[N];
@@ -177,7 +178,6 @@ __device__ __forceinline__ void project_group(const ProjDesc& P, const RowSeed* 
 
 // The same bins on a handle without a seed table: bisection between the outer boundaries.
 __device__ __forceinline__ int32_t pixel_of_bisect(const ProjDesc& P, float x, float y, float z,
-                                                   uint32_t i,
                                                    uint32_t* __restrict__ keys) {
     const float rho2 = __fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y));
     const float rg = __fsqrt_rn(__fadd_rn(rho2, __fmul_rn(z, z)));
@@ -204,10 +204,10 @@ __device__ __forceinline__ int32_t project_one(const ProjDesc& P, const RowSeed*
                                                const float* __restrict__ xyz, int64_t i,
                                                uint32_t* __restrict__ keys) {
     const float x = __ldg(xyz + 3 * i), y = __ldg(xyz + 3 * i + 1), z = __ldg(xyz + 3 * i + 2);
-    if (!(P.rs_inv_dt > 0.0f)) return pixel_of_bisect(P, x, y, z, (uint32_t)i, keys);
+    if (!(P.rs_inv_dt > 0.0f)) return pixel_of_bisect(P, x, y, z, keys);
     const float xs[1] = {x}, ys[1] = {y}, zs[1] = {z};
     int32_t out[1];
-    project_group<1>(P, seeds, xs, ys, zs, (uint32_t)i, keys, out);
+    project_group<1>(P, seeds, xs, ys, zs, keys, out);
     return out[0];
 }
 
@@ -248,7 +248,7 @@ __device__ __forceinline__ void project_points(const ProjDesc& P, const RowSeed*
             const float ys[4] = {a.y, b.x, b.w, c.z};
             const float zs[4] = {a.z, b.y, c.x, c.w};
             int32_t o[4];
-            project_group<4>(P, seeds, xs, ys, zs, (uint32_t)(4 * g), keys, o);
+            project_group<4>(P, seeds, xs, ys, zs, keys, o);
             reinterpret_cast<int4*>(point_pixel)[g] = make_int4(o[0], o[1], o[2], o[3]);
             a = na;
             b = nb;

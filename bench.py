@@ -584,6 +584,45 @@ def main():
         "note": "relabel of the c4 batch's labels: components under 100 px dropped, the rest "
                 "numbered 0..N-1 by minimum index; timed alone, after a fresh labelling"}
 
+    # ---- labelling and the filter in one call (flic_label_filter_batch: sizes counted
+    # inside the labelling kernel, no size histogram), against the two calls back to back
+    # and the labelling alone; each queued behind a spin kernel so that the events time
+    # the device
+    modes = ("label", "separate", "fused")
+    pair_ms = {m: [] for m in modes}
+    pair_ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    for rep in range(69):
+        k = rep % NCOPIES
+        mode = modes[rep % 3]
+        host_ahead(torch, stream, 1000.0)
+        pair_ev[0].record(stream)
+        if mode == "fused":
+            flic.flic_label_filter_batch(batches[k], bargs[k], 100, rl_num, stream)
+        else:
+            flic.flic_label_batch(batches[k], bargs[k], stream)
+            if mode == "separate":
+                flic.flic_filter_relabel_batch(batches[k], bargs[k], 100, rl_num, stream)
+        pair_ev[1].record(stream)
+        torch.cuda.synchronize()
+        if rep >= 9:
+            pair_ms[mode].append(pair_ev[0].elapsed_time(pair_ev[1]))
+    lab_ms = statistics.median(pair_ms["label"])
+    sep_ms = statistics.median(pair_ms["separate"])
+    fused_ms = statistics.median(pair_ms["fused"])
+    label_filter = {
+        "min_size": 100,
+        "label_ms_per_batch": round(lab_ms, 4),
+        "separate_ms_per_batch": round(sep_ms, 4),
+        "fused_ms_per_batch": round(fused_ms, 4),
+        "filter_share_separate_ms": round(sep_ms - lab_ms, 4),
+        "filter_share_fused_ms": round(fused_ms - lab_ms, 4),
+        "fused_mpixel_per_s": round(total_px / (fused_ms / 1e3) / 1e6, 1),
+        "launches_separate": 7, "launches_fused": 5,
+        "note": "label + cluster filter of the c4 batch: flic_label_batch then "
+                "flic_filter_relabel_batch, against flic_label_filter_batch (component sizes "
+                "counted in the labelling kernel; the zeroing and histogram launches go); the "
+                "filter shares subtract the labelling alone, timed the same way"}
+
     # ---- ground extraction (§III-A, 10 degrees, height line 1.7 m) fused into the same
     # batched labelling: the batch timed again with the ground removed first
     for h in handles:
@@ -870,6 +909,7 @@ def main():
             "projection_batch": projection_batch,
             "edges": edges,
             "cluster_filter": cluster_filter,
+            "label_filter": label_filter,
             "ground_extraction": ground_extraction,
             "segmentation_quality": seg,
             "serving": serving,

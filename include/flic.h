@@ -366,6 +366,24 @@ flic_status flic_filter_relabel_batch(flic_batch b, const flic_handle* hs,
                                       int32_t* num_out, void* stream);
 
 /*
+ * flic_label_filter_batch — flic_label_batch followed by flic_filter_relabel_batch on the
+ * same frames, with the component sizes counted by the labelling kernel itself: each
+ * strip counts the pixels of its strip-local components from its runs (a run's length is
+ * one bit scan of its edge words) and, after the border merges, adds the count of every
+ * root that a merge hooked into its component's root.  The relabel step then reads only
+ * the roots' counts and skips the size histogram over the labels.  Arguments as the two
+ * calls: frame i has hs[i]'s shape, ranges[i] (device float32, read) and labels[i]
+ * (device int32, written: after the call -1 or the component's id 0..N-1); num_out a
+ * device int32 array of nframes or NULL.  Uses the batch's relabel scratch (8 bytes per
+ * pixel, grown on demand).  The result equals flic_label_batch + flic_filter_relabel_batch.
+ * Errors: those of the two calls.
+ */
+flic_status flic_label_filter_batch(flic_batch b, const flic_handle* hs,
+                                    const float* const* ranges, int32_t* const* labels,
+                                    int32_t nframes, int32_t min_size, int32_t* num_out,
+                                    void* stream);
+
+/*
  * flic_device_status — synchronise the device, read and (if clear != 0) reset the
  * handle's device error word.  Returns FLIC_OK; FLIC_ERR_TIMEOUT when a bounded loop in a
  * kernel gave up since the last reset (labels of that call are then not valid); or

@@ -180,7 +180,7 @@ struct flic_batch_ctx {
     bool pending = false;
     cudaStream_t cap_stream = nullptr;
     Tuning tune;
-    std::map<std::tuple<int, int, size_t>, cudaGraphExec_t> graphs;  // grid, threads, smem
+    std::map<std::tuple<int, int, size_t, bool>, cudaGraphExec_t> graphs;  // grid, threads, smem, counting
     int last_info[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // the previous call's arguments and launch shape: an identical call replays the graph
     std::vector<const void*> last_args;
@@ -826,8 +826,15 @@ flic_status flic_batch_last_plan(flic_batch b, int32_t* info) {
     return FLIC_OK;
 }
 
-flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* const* ranges,
-                             int32_t* const* labels, int32_t nframes, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// flic_label_batch, and the labelling step of flic_label_filter_batch: with cnts and roots
+// (one each per frame) the kernel also counts the components' sizes (FrameDesc::cnt).
+flic_status label_batch_impl(flic_batch b, const flic_handle* hs, const float* const* ranges,
+                             int32_t* const* labels, int32_t nframes, void* stream,
+                             int32_t* const* cnts, uint32_t* const* roots) {
     if (!b) return fail(FLIC_ERR_INVALID, "NULL batch");
     if (nframes < 0) return fail(FLIC_ERR_INVALID, "nframes < 0");
     if (nframes == 0) return FLIC_OK;
@@ -845,12 +852,14 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
 
     // identical to the previous call (same handles, buffers, tuning): replay the graph
     std::vector<const void*> args;
-    args.reserve((size_t)4 * nframes);
+    args.reserve((size_t)6 * nframes);
     for (int i = 0; i < nframes; ++i) {
         args.push_back((const void*)(uintptr_t)hs[i]->uid);
         args.push_back((const void*)(uintptr_t)hs[i]->version);
         args.push_back(ranges[i]);
         args.push_back(labels[i]);
+        args.push_back(cnts ? cnts[i] : nullptr);
+        args.push_back(roots ? roots[i] : nullptr);
     }
     if (b->last_exec && args == b->last_args) {
         // the queue counters are shared with the previous launch: order after it
@@ -881,6 +890,10 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
         smem = std::max(smem, plans[i].smem);
         total_strips += plans[i].nstrips;
         b->h_frames[i] = frame_desc(h, ranges[i], labels[i], plans[i]);
+        if (cnts) {
+            b->h_frames[i].cnt = cnts[i];
+            b->h_frames[i].roots = roots[i];
+        }
     }
     smem = std::max(smem, b->min_smem);
     const int resident = resident_blocks(t.threads, smem, t.ctas_per_sm);
@@ -938,7 +951,7 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
     b->pending = true;
 
     // the persistent kernel, captured once per launch shape and replayed
-    auto key = std::make_tuple(grid, t.threads, smem);
+    auto key = std::make_tuple(grid, t.threads, smem, cnts != nullptr);
     auto found = b->graphs.find(key);
     cudaGraphExec_t exec = nullptr;
     if (found != b->graphs.end()) {
@@ -952,7 +965,8 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
         L.tasks = b->d_tasks;
         L.dims = b->d_dims;
         L.counters = b->d_counters;
-        cudaError_t le = flic::launch_label(L, grid, t.threads, smem, b->cap_stream);
+        cudaError_t le = flic::launch_label(L, grid, t.threads, smem, b->cap_stream,
+                                            cnts != nullptr);
         e = cudaStreamEndCapture(b->cap_stream, &graph);
         if (le != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -974,6 +988,15 @@ flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* c
                    resident};
     std::memcpy(b->last_info, info, sizeof(info));
     return FLIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+flic_status flic_label_batch(flic_batch b, const flic_handle* hs, const float* const* ranges,
+                             int32_t* const* labels, int32_t nframes, void* stream) {
+    return label_batch_impl(b, hs, ranges, labels, nframes, stream, nullptr, nullptr);
 }
 
 // ------------------------------------------------------------------ batch from host memory
@@ -1179,14 +1202,15 @@ flic_status flic_filter_relabel(flic_handle h, int32_t* labels, int32_t min_size
     return FLIC_OK;
 }
 
-flic_status flic_filter_relabel_batch(flic_batch b, const flic_handle* hs,
-                                      int32_t* const* labels, int32_t nframes, int32_t min_size,
-                                      int32_t* num_out, void* stream) {
-    if (!b || !hs || !labels) return fail(FLIC_ERR_INVALID, "NULL argument");
-    if (nframes < 0 || nframes > b->max_frames)
-        return fail(FLIC_ERR_INVALID, "nframes must be 0..%d", b->max_frames);
-    if (nframes == 0) return FLIC_OK;
-    cudaStream_t st = (cudaStream_t)stream;
+}  // extern "C"
+
+namespace {
+
+// The relabel launch of nframes frames: scratch (grown when needed), per-frame descriptors
+// and the tile map, uploaded on the stream after the previous relabel of this batch.
+flic_status relabel_prepare(flic_batch b, const flic_handle* hs, int32_t* const* labels,
+                            int32_t nframes, int32_t min_size, int32_t* num_out,
+                            cudaStream_t st, flic::RelabelLaunch* out) {
     cudaError_t e;
     size_t npix_all = 0;
     int ntiles = 0;
@@ -1246,8 +1270,62 @@ flic_status flic_filter_relabel_batch(flic_batch b, const flic_handle* hs,
     L.ntiles = ntiles;
     L.min_size = min_size;
     carve_relabel(&L, b->d_rl_scratch, npix_all, ntiles);
-    e = flic::launch_relabel(L, st);
+    *out = L;
+    return FLIC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+flic_status flic_filter_relabel_batch(flic_batch b, const flic_handle* hs,
+                                      int32_t* const* labels, int32_t nframes, int32_t min_size,
+                                      int32_t* num_out, void* stream) {
+    if (!b || !hs || !labels) return fail(FLIC_ERR_INVALID, "NULL argument");
+    if (nframes < 0 || nframes > b->max_frames)
+        return fail(FLIC_ERR_INVALID, "nframes must be 0..%d", b->max_frames);
+    if (nframes == 0) return FLIC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    flic::RelabelLaunch L{};
+    flic_status fs = relabel_prepare(b, hs, labels, nframes, min_size, num_out, st, &L);
+    if (fs != FLIC_OK) return fs;
+    cudaError_t e = flic::launch_relabel(L, st);
     if (e != cudaSuccess) return cuda_fail(e, "flic_filter_relabel_batch launch");
+    if ((e = cudaEventRecord(b->rl_done, st)) != cudaSuccess) return cuda_fail(e, "event record");
+    return FLIC_OK;
+}
+
+flic_status flic_label_filter_batch(flic_batch b, const flic_handle* hs,
+                                    const float* const* ranges, int32_t* const* labels,
+                                    int32_t nframes, int32_t min_size, int32_t* num_out,
+                                    void* stream) {
+    if (!b || !hs || !ranges || !labels) return fail(FLIC_ERR_INVALID, "NULL argument");
+    if (nframes < 0 || nframes > b->max_frames)
+        return fail(FLIC_ERR_INVALID, "nframes must be 0..%d", b->max_frames);
+    if (nframes == 0) return FLIC_OK;
+    for (int i = 0; i < nframes; ++i)
+        if (!hs[i] || !ranges[i] || !labels[i])
+            return fail(FLIC_ERR_INVALID, "frame %d: NULL handle or buffer", i);
+    cudaStream_t st = (cudaStream_t)stream;
+    flic::RelabelLaunch L{};
+    flic_status fs = relabel_prepare(b, hs, labels, nframes, min_size, num_out, st, &L);
+    if (fs != FLIC_OK) return fs;
+    // the root bitmask is built by the labeller's atomics: zero it first (the scratch is
+    // the relabel's, ordered after the previous relabel by relabel_prepare)
+    cudaError_t e = cudaMemsetAsync(L.roots, 0,
+                                    (size_t)L.ntiles * (flic::kRelabelTile / 32) * sizeof(uint32_t),
+                                    st);
+    if (e != cudaSuccess) return cuda_fail(e, "root bitmask clear");
+    std::vector<int32_t*> cnts(nframes);
+    std::vector<uint32_t*> roots(nframes);
+    for (int i = 0; i < nframes; ++i) {
+        cnts[i] = b->h_rl[i].cnt;
+        roots[i] = L.roots + (size_t)b->h_rl[i].tile0 * (flic::kRelabelTile / 32);
+    }
+    fs = label_batch_impl(b, hs, ranges, labels, nframes, stream, cnts.data(), roots.data());
+    if (fs != FLIC_OK) return fs;
+    e = flic::launch_relabel(L, st, /*counted=*/true);
+    if (e != cudaSuccess) return cuda_fail(e, "flic_label_filter_batch relabel launch");
     if ((e = cudaEventRecord(b->rl_done, st)) != cudaSuccess) return cuda_fail(e, "event record");
     return FLIC_OK;
 }

@@ -44,6 +44,10 @@ struct FrameDesc {
     const float* gnd;
     float gnd_tan;        // tan(theta), for the height line
     float gnd_height;     // mount height (m); <= 0: no height exception
+    // component sizes for flic_label_filter_batch (nullptr: not counted): the size of each
+    // component lands at its root's index in cnt, and its root's bit in roots (zero on entry)
+    int32_t* cnt;
+    uint32_t* roots;
 };
 constexpr int kGroundFields = 8;  // floats per row of the ground table (6 used)
 
@@ -124,11 +128,14 @@ struct RelabelLaunch {
 inline size_t relabel_scratch_ints(size_t npix_all, size_t ntiles) {
     return npix_all + 2 * ntiles * (kRelabelTile / 32) + 2 * ntiles;
 }
-cudaError_t launch_relabel(const RelabelLaunch& L, cudaStream_t stream);
+// counted: the sizes at the roots and the root bitmask are already there (the labeller
+// counted them, FrameDesc::cnt): only count, scan, assign and apply run.
+cudaError_t launch_relabel(const RelabelLaunch& L, cudaStream_t stream, bool counted = false);
 
 // Kernel launchers (flic_label.cu / flic_project.cu).  Return cudaGetLastError().
+// count: the instance that counts component sizes (frames with FrameDesc::cnt set).
 cudaError_t launch_label(const LabelLaunch& L, int grid, int threads, size_t smem,
-                         cudaStream_t stream);
+                         cudaStream_t stream, bool count = false);
 cudaError_t label_blocks_per_sm(int threads, size_t smem, int* out);
 cudaError_t launch_edges(const FrameDesc& f, uint16_t* mask, cudaStream_t stream);
 cudaError_t label_kernel_setup(size_t max_smem);

@@ -693,6 +693,108 @@ __device__ void write_labels(const Strip& s, const Carve& sm) {
     }
 }
 
+// f. Component sizes for the cluster filter (FrameDesc::cnt), after the labels are out:
+//    every strip-local root's pixel count, stored at its global index, and its bit in the
+//    frame's root bitmask.  The parent entries of the roots become counters, -1 - count (the
+//    forest is no longer read): a run start whose entry is negative is a root.  A run is its
+//    start and the pixels after it that offset-1 edges join (runs end at their 32-column
+//    segment).  One thread per row segment; np = 2S + 1 ballot words per segment.  Inlined
+//    (as count_strip): an ABI call in this kernel costs far more than the work (measured).
+__device__ __forceinline__ void count_runs(const unsigned* w, int* par, int S, int R, int sh,
+                                        int W, int C, int c0, int32_t* cnt, uint32_t* roots) {
+    const int np = 2 * S + 1;
+    const int n = R << (sh - 5);
+    const int nsl = sh - 5;
+    auto starts = [&](int u) { return w[u * np] & ~(w[u * np + 1] << 1); };
+    for (int u = threadIdx.x; u < n; u += blockDim.x) {
+        if (((u & ((1 << nsl) - 1)) << 5) >= W) continue;  // segment past the strip
+        unsigned x = starts(u);
+        while (x) {
+            const int c = (u << 5) + __ffs(x) - 1;
+            x &= x - 1u;
+            if (par[slot(c)] == c) par[slot(c)] = -1;
+        }
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < n; u += blockDim.x) {
+        if (((u & ((1 << nsl) - 1)) << 5) >= W) continue;
+        const unsigned ends = ~w[u * np + 1] | 0x80000000u;  // no offset-1 edge to the right
+        unsigned x = starts(u);
+        int acc_root = -1, acc = 0;  // consecutive runs of one root, summed first
+        while (x) {
+            const int b = __ffs(x) - 1;
+            x &= x - 1u;
+            const int c = (u << 5) + b;
+            const int len = __ffs(ends >> b);  // pixels b .. the first end at or after b
+            const int p = par[slot(c)];
+            const int root = p < 0 ? c : p;
+            if (root != acc_root) {
+                if (acc) atomicSub(par + slot(acc_root), acc);
+                acc_root = root;
+                acc = 0;
+            }
+            acc += len;
+        }
+        if (acc) atomicSub(par + slot(acc_root), acc);
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < n; u += blockDim.x) {
+        if (((u & ((1 << nsl) - 1)) << 5) >= W) continue;
+        unsigned x = starts(u);
+        while (x) {
+            const int c = (u << 5) + __ffs(x) - 1;
+            x &= x - 1u;
+            const int p = par[slot(c)];
+            if (p < 0) {
+                const int g = (c >> sh) * C + c0 + (c & ((1 << sh) - 1));
+                cnt[g] = -1 - p;
+                atomicOr(roots + (g >> 5), 1u << (g & 31));
+            }
+        }
+    }
+}
+
+// The strip si of frame f.
+__device__ __forceinline__ Strip strip_of(const FrameDesc& f, int si) {
+    Strip s{};
+    s.range = f.range;
+    s.labels = f.labels;
+    s.kv = f.kv;
+    s.kh = f.kh;
+    s.kd = f.kd;
+    s.status = f.status;
+    s.R = f.rows;
+    s.C = f.cols;
+    s.S = f.skip;
+    s.delta2 = f.delta2;
+    s.wrap = f.wrap != 0;
+    s.c0 = si * f.strip_w;
+    s.W = min(f.strip_w, s.C - s.c0);
+    s.sh = f.pitch_log2;
+    s.RP = (s.W + s.S + 3) & ~3;
+    s.bulk = ((s.C & 3) == 0) && ((s.c0 & 3) == 0) && ((s.W & 3) == 0) &&
+             ((reinterpret_cast<uintptr_t>(s.range) & 15) == 0);
+    s.limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
+    s.gnd = f.rows >= 2 ? f.gnd : nullptr;
+    s.gnd_tan = f.gnd_tan;
+    s.gnd_height = f.gnd_height;
+    s.lattice = f.lattice != 0;
+    return s;
+}
+
+// Step f for strip si of frame fi of a batch, after its strip pass (the forest and the
+// ballot words still in shared memory); nothing when the frame is not counted.
+__device__ __forceinline__ void count_strip(const FrameDesc* frames, int fi, int si,
+                                         unsigned char* base) {
+    if (!frames) return;
+    const FrameDesc f = frames[fi];
+    if (!f.cnt) return;
+    const Strip s = strip_of(f, si);
+    const Carve sm = carve(base, s);
+    __syncthreads();  // the labels are out
+    count_runs(sm.words, sm.par, s.S, s.R, s.sh, s.W, s.C, s.c0, f.cnt, f.roots);
+}
+
 // Steps 1 and a to e of a staged strip.
 template <int S, bool D>
 __device__ void phase1_strip(const Strip& s, const Carve& sm) {
@@ -939,6 +1041,41 @@ __device__ __forceinline__ unsigned dynamic_smem_bytes() {
     return v;
 }
 
+// With component sizes (FrameDesc::cnt): each strip-local root of this strip that a border
+// merge hooked adds its count to its component's root and leaves the root bitmask, so that
+// afterwards the bitmask holds the components' minima and cnt their sizes.  One thread per
+// bitmask word of the strip (rows x the words of a row's columns c0 .. c0 + W - 1), all
+// loads of the block in flight at once.  Inlined: a real call here costs far more than
+// the work (measured).
+__device__ __forceinline__ void phase3_counts(int32_t* labels, int32_t* cnt, uint32_t* roots,
+                                              int32_t* status, int rows, int cols, int c0,
+                                              int W, int limit) {
+    const int per_row = ((c0 + W - 1) >> 5) - (c0 >> 5) + 2;  // >= the words a row touches
+    const int n = rows * per_row;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int r = i / per_row;
+        const int p_first = r * cols + c0, p_last = p_first + W - 1;
+        const int w = (p_first >> 5) + (i - r * per_row);
+        if (w > (p_last >> 5)) continue;
+        unsigned bits = __ldcg(roots + w);
+        if (w == (p_first >> 5)) bits &= ~0u << (p_first & 31);
+        if (w == (p_last >> 5)) bits &= (2u << (p_last & 31)) - 1u;
+        while (bits) {
+            const int b = __ffs(bits) - 1;
+            bits &= bits - 1u;
+            const int l = (w << 5) + b;
+            int budget = limit;
+            const int root = find_global(labels, l, budget, false);
+            if (budget <= 0) report_timeout(status);
+            if (root != l) {
+                atomicAdd(cnt + root, __ldcg(cnt + l));
+                atomicAnd(roots + w, ~(1u << b));
+            }
+        }
+    }
+}
+
+template <bool kCount>
 __device__ void phase3_strip(const FrameDesc& f, int si, unsigned long long* cache) {
     constexpr int G = 4;
     const int lane = threadIdx.x & 31;
@@ -1016,6 +1153,8 @@ __device__ void phase3_strip(const FrameDesc& f, int si, unsigned long long* cac
             }
         }
     }
+    if (kCount && f.cnt)
+        phase3_counts(f.labels, f.cnt, f.roots, f.status, f.rows, f.cols, c0, W, limit);
 }
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -1028,6 +1167,9 @@ __device__ __forceinline__ void red_release_add(int* p, int v) {
     asm volatile("red.release.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// kCount: the instance that also counts component sizes (FrameDesc::cnt); the plain
+// instance has no trace of it.
+template <bool kCount>
 __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t tma_bar;
@@ -1064,33 +1206,13 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
         int* done_ctr = L.counters + kCtrFrames + kCtrPerFrame * fi;
 
         if (kind == kTaskP1) {
-            Strip s{};
-            s.range = f.range;
-            s.labels = f.labels;
-            s.kv = f.kv;
-            s.kh = f.kh;
-            s.kd = f.kd;
-            s.status = f.status;
-            s.R = f.rows;
-            s.C = f.cols;
-            s.S = f.skip;
-            s.delta2 = f.delta2;
-            s.wrap = f.wrap != 0;
-            s.c0 = si * f.strip_w;
-            s.W = min(f.strip_w, s.C - s.c0);
-            s.sh = f.pitch_log2;
-            s.RP = (s.W + s.S + 3) & ~3;
-            s.bulk = ((s.C & 3) == 0) && ((s.c0 & 3) == 0) && ((s.W & 3) == 0) &&
-                     ((reinterpret_cast<uintptr_t>(s.range) & 15) == 0);
-            s.limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
-            s.gnd = f.rows >= 2 ? f.gnd : nullptr;
-            s.gnd_tan = f.gnd_tan;
-            s.gnd_height = f.gnd_height;
-            s.lattice = f.lattice != 0;
+            const Strip s = strip_of(f, si);
             const Carve sm = carve(smem_raw, s);
             phase1_stage(s, sm, &tma_bar, parity);
             if (s.bulk) parity ^= 1u;
             phase1(s, sm);
+            // (from the descriptor in global memory: nothing of the strip pass stays live)
+            if (kCount) count_strip(L.frames, fi, si, smem_raw);
             if (border) {
                 // arrive at the (up to two) borders of this strip (both arrivals at once,
                 // by two threads); the second arrival at a border merges it.  A merged
@@ -1137,7 +1259,7 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
                 }
             }
             __syncthreads();
-            if (flag_sh) phase3_strip(f, si, reinterpret_cast<unsigned long long*>(smem_raw));
+            if (flag_sh) phase3_strip<kCount>(f, si, reinterpret_cast<unsigned long long*>(smem_raw));
         }
         __syncthreads();  // shared memory is reused by the next task
     }
@@ -1309,18 +1431,33 @@ __global__ void flic_edges_kernel(const FrameDesc f, uint16_t* __restrict__ mask
 }  // namespace
 
 cudaError_t label_kernel_setup(size_t max_smem) {
-    return cudaFuncSetAttribute(flic_label_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)max_smem);
+    cudaError_t e = cudaFuncSetAttribute(flic_label_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)max_smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(flic_label_kernel<true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)max_smem);
+    return e;
 }
 
 cudaError_t launch_label(const LabelLaunch& L, int grid, int threads, size_t smem,
-                         cudaStream_t stream) {
-    flic_label_kernel<<<grid, threads, smem, stream>>>(L);
+                         cudaStream_t stream, bool count) {
+    if (count)
+        flic_label_kernel<true><<<grid, threads, smem, stream>>>(L);
+    else
+        flic_label_kernel<false><<<grid, threads, smem, stream>>>(L);
     return cudaGetLastError();
 }
 
 cudaError_t label_blocks_per_sm(int threads, size_t smem, int* out) {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, flic_label_kernel, threads, smem);
+    int a = 0, b = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, flic_label_kernel<false>,
+                                                                  threads, smem);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, flic_label_kernel<true>, threads,
+                                                          smem);
+    *out = a < b ? a : b;  // one grid size serves both instances
+    return e;
 }
 
 // One resident wave of 128-thread blocks (grid-stride over the tiles): no second partial

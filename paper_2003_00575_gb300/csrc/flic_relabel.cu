@@ -297,11 +297,18 @@ cudaError_t launch_dependent(void (*kernel)(const RelabelLaunch), int grid,
 
 }  // namespace
 
-cudaError_t launch_relabel(const RelabelLaunch& L, cudaStream_t stream) {
+cudaError_t launch_relabel(const RelabelLaunch& L, cudaStream_t stream, bool counted) {
     if (L.ntiles <= 0) return cudaSuccess;
-    cudaError_t e = launch_dependent(relabel_zero, L.ntiles, L, stream);
-    if (e == cudaSuccess) e = launch_dependent(relabel_hist, L.ntiles, L, stream);
-    if (e == cudaSuccess) e = launch_dependent(relabel_count, L.ntiles, L, stream);
+    cudaError_t e;
+    if (counted) {
+        // after the labeller's graph: an ordinary stream-ordered launch (its wait is a no-op)
+        relabel_count<<<L.ntiles, kThreads, 0, stream>>>(L);
+        e = cudaGetLastError();
+    } else {
+        e = launch_dependent(relabel_zero, L.ntiles, L, stream);
+        if (e == cudaSuccess) e = launch_dependent(relabel_hist, L.ntiles, L, stream);
+        if (e == cudaSuccess) e = launch_dependent(relabel_count, L.ntiles, L, stream);
+    }
     if (e == cudaSuccess) e = launch_dependent(relabel_scan, L.nframes, L, stream);
     if (e == cudaSuccess) e = launch_dependent(relabel_assign, L.ntiles, L, stream);
     if (e == cudaSuccess) e = launch_dependent(relabel_apply, L.ntiles, L, stream);

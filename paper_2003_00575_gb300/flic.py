@@ -59,6 +59,7 @@ SIGNATURES = {
     "flic_set_ground": (_I32, [_P, _F64, _F64]),
     "flic_filter_relabel": (_I32, [_P, _P, _I32, _P, _P]),
     "flic_filter_relabel_batch": (_I32, [_P, _P, _P, _I32, _I32, _P, _P]),
+    "flic_label_filter_batch": (_I32, [_P, _P, _P, _P, _I32, _I32, _P, _P]),
     "flic_batch_create": (_I32, [_I32, _P]),
     "flic_label_batch": (_I32, [_P, _P, _P, _P, _I32, _P]),
     "flic_label_batch_host": (_I32, [_P, _P, _I32, _P, _P, _I32, _U32, _P]),
@@ -405,6 +406,16 @@ def flic_filter_relabel_batch(b: Batch, args: BatchArgs, min_size: int, num_out=
     """flic_filter_relabel over the frames of args (their labels buffers) in one go."""
     _check(_lib.flic_filter_relabel_batch(
         b.ptr, args.hs, args.ls, args.n, int(min_size),
+        None if num_out is None else _dptr(num_out, "int32", args.n, "num_out"),
+        _stream(stream)))
+
+
+def flic_label_filter_batch(b: Batch, args: BatchArgs, min_size: int, num_out=None,
+                            stream=None) -> None:
+    """flic_label_batch then flic_filter_relabel_batch over args, the sizes counted while
+    labelling (one call; the labels buffers receive the kept components' ids or -1)."""
+    _check(_lib.flic_label_filter_batch(
+        b.ptr, args.hs, args.rs, args.ls, args.n, int(min_size),
         None if num_out is None else _dptr(num_out, "int32", args.n, "num_out"),
         _stream(stream)))
 

@@ -58,6 +58,8 @@ def test_invalid_arguments_rejected_without_gpu(lib_path):
     assert lib.flic_destroy(None) == flic.FLIC_OK
     assert lib.flic_batch_destroy(None) == flic.FLIC_OK
     assert lib.flic_label_batch_host(None, None, 1, None, None, 0, 0, None) == flic.FLIC_ERR_INVALID
+    assert lib.flic_label_filter_batch(None, None, None, None, 1, 100, None, None) == flic.FLIC_ERR_INVALID
+    assert lib.flic_filter_relabel_batch(None, None, None, 1, 100, None, None) == flic.FLIC_ERR_INVALID
 
 
 def test_product_path_does_not_import_the_oracle():

@@ -123,9 +123,13 @@ def run_step(flic, srv, pool: FramePool, rate: float, seconds: float, seed: int)
     try:
         t_start = time.perf_counter()
         c0 = flic.flic_server_clock()
+        late = np.empty(len(sched))  # how far behind its schedule each submission was
         for i, (t, s, kind) in enumerate(sched):
-            while time.perf_counter() - t_start < t:
-                pass
+            while True:
+                now = time.perf_counter() - t_start
+                if now >= t:
+                    break
+            late[i] = now - t
             x, y = pool.pick(s, kind)
             if flic.flic_server_submit(srv, s, kind, x, y, i) != flic.FLIC_OK:
                 rejected += 1
@@ -138,6 +142,12 @@ def run_step(flic, srv, pool: FramePool, rate: float, seconds: float, seed: int)
     c1 = max([r.t_done for r in records], default=c0)
     out = summarize(records, c0, c1)
     out.update({"rate_offered": round(rate, 1), "submitted": len(sched), "rejected": rejected})
+    if len(sched):
+        # the load generator's own delays: a submission made late by a pause of this
+        # thread arrives in a burst with the ones due during the pause
+        out.update({"submit_late_ms_p99": round(float(np.percentile(late, 99)) * 1e3, 3),
+                    "submit_late_ms_max": round(float(late.max()) * 1e3, 3),
+                    "submit_late_over_1ms": int((late > 1e-3).sum())})
     return out
 
 

@@ -149,24 +149,33 @@ __global__ void __launch_bounds__(kThreads) relabel_hist(const RelabelLaunch L) 
         if (keys[i] >= 0) atomicAdd(F.cnt + keys[i], vals[i]);
 }
 
-// Threads 0..127 take one bitmask word each.
+// Two tiles per block: threads 0..127 take the words of tile 2b, threads 128..255 those
+// of tile 2b + 1, one bitmask word each (a block per tile left half of its threads idle).
+__device__ __forceinline__ int pair_tile(int& wi) {
+    const int half = threadIdx.x / kWords;
+    wi = threadIdx.x - half * kWords;
+    return 2 * blockIdx.x + half;
+}
+
 __global__ void __launch_bounds__(kThreads) relabel_count(const RelabelLaunch L) {
     wait_prior_grid();
     __shared__ int red[kThreads / 32];
-    const int t = blockIdx.x;
-    const RelabelFrame F = frame_at(L, frame_of_tile(L, t));
-    const int p0 = (t - F.tile0) * kRelabelTile;
+    int wi;
+    const int t = pair_tile(wi);
+    const bool live = t < L.ntiles;
     int c = 0;
-    if (threadIdx.x < kWords) {
-        const unsigned r = __ldcg(L.roots + (size_t)t * kWords + threadIdx.x);
+    if (live) {
+        const RelabelFrame F = frame_at(L, frame_of_tile(L, t));
+        const int p0 = (t - F.tile0) * kRelabelTile;
+        const unsigned r = __ldcg(L.roots + (size_t)t * kWords + wi);
         unsigned k = 0;
         if (r) {  // the counts of the word's roots, all loads in flight at once
-            const int32_t* wc = F.cnt + p0 + 32 * threadIdx.x;
+            const int32_t* wc = F.cnt + p0 + 32 * wi;
 #pragma unroll
             for (int b = 0; b < 32; ++b)
                 if (((r >> b) & 1u) && __ldcg(wc + b) >= L.min_size) k |= 1u << b;
         }
-        __stcg(L.kept + (size_t)t * kWords + threadIdx.x, k);
+        __stcg(L.kept + (size_t)t * kWords + wi, k);
         c = __popc(k);
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -174,9 +183,10 @@ __global__ void __launch_bounds__(kThreads) relabel_count(const RelabelLaunch L)
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(kFull, c, o);
     if (lane == 0) red[warp] = c;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (wi == 0 && live) {  // the first thread of each half sums its tile's four warps
+        constexpr int kWarpsPerTile = kWords / 32;
         int s = 0;
-        for (int w = 0; w < kThreads / 32; ++w) s += red[w];
+        for (int w = 0; w < kWarpsPerTile; ++w) s += red[warp + w];
         L.tile_cnt[t] = s;
     }
 }
@@ -206,20 +216,26 @@ __global__ void __launch_bounds__(kThreads) relabel_scan(const RelabelLaunch L) 
     if (threadIdx.x == kThreads - 1 && F.num_out) *F.num_out = part[kThreads - 1];
 }
 
-// Threads 0..127 take one word each: an exclusive prefix of the kept counts over the words
-// (raster order), then every root of the word gets its rank, or -1.
+// Two tiles per block as in relabel_count, one word per thread: an exclusive prefix of the
+// kept counts over the tile's words (raster order), then every root of the word gets its
+// rank, or -1.
 __global__ void __launch_bounds__(kThreads) relabel_assign(const RelabelLaunch L) {
     wait_prior_grid();
+    constexpr int kWarpsPerTile = kWords / 32;
     __shared__ int red[kThreads / 32];
     __shared__ int warp_off[kThreads / 32];
-    const int t = blockIdx.x;
-    const RelabelFrame F = frame_at(L, frame_of_tile(L, t));
-    const int p0 = (t - F.tile0) * kRelabelTile;
+    int wi;
+    const int t = pair_tile(wi);
+    const bool live = t < L.ntiles;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    RelabelFrame F{};
+    int p0 = 0;
     unsigned r = 0, k = 0;
-    if (threadIdx.x < kWords) {
-        r = __ldcg(L.roots + (size_t)t * kWords + threadIdx.x);
-        k = __ldcg(L.kept + (size_t)t * kWords + threadIdx.x);
+    if (live) {
+        F = frame_at(L, frame_of_tile(L, t));
+        p0 = (t - F.tile0) * kRelabelTile;
+        r = __ldcg(L.roots + (size_t)t * kWords + wi);
+        k = __ldcg(L.kept + (size_t)t * kWords + wi);
     }
     const int c = __popc(k);
     int incl = c;
@@ -230,20 +246,21 @@ __global__ void __launch_bounds__(kThreads) relabel_assign(const RelabelLaunch L
     }
     if (lane == 31) red[warp] = incl;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (wi == 0) {  // the first thread of each half: its tile's warp offsets
         int s = 0;
-        for (int w = 0; w < kThreads / 32; ++w) {
+        for (int w = warp; w < warp + kWarpsPerTile; ++w) {
             warp_off[w] = s;
             s += red[w];
         }
     }
     __syncthreads();
+    if (!live) return;
     const int base = L.tile_off[t] + warp_off[warp] + incl - c;
     while (r) {
         const int b = __ffs(r) - 1;
         r &= r - 1u;
         const bool kb = (k >> b) & 1u;
-        __stcg(F.cnt + p0 + 32 * threadIdx.x + b, kb ? base + __popc(k & ((1u << b) - 1u)) : -1);
+        __stcg(F.cnt + p0 + 32 * wi + b, kb ? base + __popc(k & ((1u << b) - 1u)) : -1);
     }
 }
 
@@ -302,15 +319,15 @@ cudaError_t launch_relabel(const RelabelLaunch& L, cudaStream_t stream, bool cou
     cudaError_t e;
     if (counted) {
         // after the labeller's graph: an ordinary stream-ordered launch (its wait is a no-op)
-        relabel_count<<<L.ntiles, kThreads, 0, stream>>>(L);
+        relabel_count<<<(L.ntiles + 1) / 2, kThreads, 0, stream>>>(L);
         e = cudaGetLastError();
     } else {
         e = launch_dependent(relabel_zero, L.ntiles, L, stream);
         if (e == cudaSuccess) e = launch_dependent(relabel_hist, L.ntiles, L, stream);
-        if (e == cudaSuccess) e = launch_dependent(relabel_count, L.ntiles, L, stream);
+        if (e == cudaSuccess) e = launch_dependent(relabel_count, (L.ntiles + 1) / 2, L, stream);
     }
     if (e == cudaSuccess) e = launch_dependent(relabel_scan, L.nframes, L, stream);
-    if (e == cudaSuccess) e = launch_dependent(relabel_assign, L.ntiles, L, stream);
+    if (e == cudaSuccess) e = launch_dependent(relabel_assign, (L.ntiles + 1) / 2, L, stream);
     if (e == cudaSuccess) e = launch_dependent(relabel_apply, L.ntiles, L, stream);
     return e;
 }

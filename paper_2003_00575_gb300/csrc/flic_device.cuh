@@ -104,14 +104,21 @@ __device__ __forceinline__ int find_global(int32_t* lab, int x, int& budget, boo
     }
 }
 
-__device__ __forceinline__ void union_global(int32_t* lab, int a, int b, int& budget) {
+// hook_rows: per strip of the frame, rows - the topmost row of a root that a union hooked
+// (atomicMax, 0: none).  A local component lies at or below its root's row, so the flatten
+// of a strip can start at that row: no label above it changes.
+__device__ __forceinline__ void union_global(int32_t* lab, int a, int b, int& budget,
+                                             int* hook_rows, int cols, int strip_w, int rows) {
     while (budget > 0) {
         a = find_global(lab, a, budget, true);
         b = find_global(lab, b, budget, true);
         if (a == b) return;
         if (a > b) { int t = a; a = b; b = t; }
         int old = atomicMin(lab + b, a);
-        if (old == b) return;
+        if (old == b) {  // root b hooked under a
+            atomicMax(hook_rows + (b % cols) / strip_w, rows - b / cols);
+            return;
+        }
         b = old;
         --budget;
     }

@@ -63,11 +63,13 @@ struct Task {
 // Queue counters (int32, zero between launches; the kernel's last block re-zeroes them):
 // [kCtrNext] next task, [kCtrExit] blocks done, then kCtrPerFrame per frame f at
 // kCtrFrames + kCtrPerFrame*f: [0] borders merged (P3 waits for all), [1] unused,
-// [2 + b] strips of border b that finished P1.
+// [2 + b] strips of border b that finished P1, [kCtrHookRows + s] rows - the topmost row
+// of a root of strip s that a border merge hooked (0: none; P3 starts at that row).
 constexpr int kCtrNext = 0;
 constexpr int kCtrExit = 1;
 constexpr int kCtrFrames = 2;
-constexpr int kCtrPerFrame = 2 + kMaxStrips;
+constexpr int kCtrHookRows = 2 + kMaxStrips;
+constexpr int kCtrPerFrame = 2 + 2 * kMaxStrips;
 __host__ __device__ inline size_t counter_ints(int nframes) {
     return size_t(kCtrFrames) + size_t(kCtrPerFrame) * size_t(nframes);
 }

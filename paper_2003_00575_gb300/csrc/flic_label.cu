@@ -860,7 +860,7 @@ __device__ __forceinline__ unsigned long long volatile_load_u64(const unsigned l
 }
 
 template <int S>
-__device__ void border_merge_s(const FrameDesc& f, int b, int limit,
+__device__ void border_merge_s(const FrameDesc& f, int* hook, int b, int limit,
                                unsigned long long* pair_set) {
     constexpr int kItems = S * (S + 1) / 2;  // (j, k) with j + k >= S
     const int lane = threadIdx.x & 31;
@@ -906,7 +906,7 @@ __device__ void border_merge_s(const FrameDesc& f, int b, int limit,
             const int h = (int)((key * 0x9E3779B97F4A7C15ull) >> 58);  // 64 entries
             if (volatile_load_u64(pair_set + h) != key) {
                 int budget = limit;
-                union_global(f.labels, ga, gb, budget);
+                union_global(f.labels, ga, gb, budget, hook, f.cols, f.strip_w, f.rows);
                 if (budget <= 0) report_timeout(f.status);
                 pair_set[h] = key;
             }
@@ -915,7 +915,7 @@ __device__ void border_merge_s(const FrameDesc& f, int b, int limit,
 }
 
 // The same for a single strip narrower than S (wrapping onto itself): plain loops.
-__device__ void border_merge_narrow(const FrameDesc& f, int limit) {
+__device__ void border_merge_narrow(const FrameDesc& f, int* hook, int limit) {
     const int R = f.rows, C = f.cols, S = f.skip;
     for (int t = threadIdx.x; t < R * C; t += blockDim.x) {
         const int r = t / C, c = t - r * C;
@@ -928,7 +928,7 @@ __device__ void border_merge_narrow(const FrameDesc& f, int limit) {
             if (d > 0.0f && edge_pred(a, d, __ldg(f.kh + r * S + k - 1), f.delta2)) {
                 int budget = limit;
                 union_global(f.labels, __ldcg(f.labels + t), __ldcg(f.labels + (size_t)r * C + tc),
-                             budget);
+                             budget, hook, f.cols, f.strip_w, f.rows);
                 if (budget <= 0) report_timeout(f.status);
             }
         }
@@ -940,7 +940,7 @@ __device__ void border_merge_narrow(const FrameDesc& f, int limit) {
 // columns of strip b, (r, x+j)-(r+k, x-k+j) down to the left from the first k columns of
 // the next strip, j = 0..k-1, columns mod cols.  Every strip is at least S wide, so such a
 // pair crosses this border only.
-__device__ void border_merge_diag(const FrameDesc& f, int b, int limit,
+__device__ void border_merge_diag(const FrameDesc& f, int* hook, int b, int limit,
                                   unsigned long long* pair_set) {
     const int R = f.rows, C = f.cols, S = f.skip;
     const int c0 = b * f.strip_w;
@@ -972,7 +972,7 @@ __device__ void border_merge_diag(const FrameDesc& f, int b, int limit,
         const int h = (int)((key * 0x9E3779B97F4A7C15ull) >> 58);
         if (volatile_load_u64(pair_set + h) == key) continue;
         int budget = limit;
-        union_global(f.labels, ga, gb, budget);
+        union_global(f.labels, ga, gb, budget, hook, f.cols, f.strip_w, f.rows);
         if (budget <= 0) report_timeout(f.status);
         pair_set[h] = key;
     }
@@ -980,7 +980,7 @@ __device__ void border_merge_diag(const FrameDesc& f, int b, int limit,
 
 // The diagonal pairs of a single strip narrower than S that wrap around the seam (the
 // edge pass records those whose far column lies inside the strip).
-__device__ void border_merge_narrow_diag(const FrameDesc& f, int limit) {
+__device__ void border_merge_narrow_diag(const FrameDesc& f, int* hook, int limit) {
     const int R = f.rows, C = f.cols, S = f.skip;
     for (int t = threadIdx.x; t < R * C; t += blockDim.x) {
         const int r = t / C, c = t - r * C;
@@ -995,7 +995,7 @@ __device__ void border_merge_narrow_diag(const FrameDesc& f, int limit) {
                 if (d > 0.0f && edge_pred(a, d, __ldg(f.kd + r * S + k - 1), f.delta2)) {
                     int budget = limit;
                     union_global(f.labels, __ldcg(f.labels + t),
-                                 __ldcg(f.labels + (size_t)(r + k) * C + tc), budget);
+                                 __ldcg(f.labels + (size_t)(r + k) * C + tc), budget, hook, f.cols, f.strip_w, f.rows);
                     if (budget <= 0) report_timeout(f.status);
                 }
             }
@@ -1003,7 +1003,7 @@ __device__ void border_merge_narrow_diag(const FrameDesc& f, int limit) {
     }
 }
 
-__device__ void border_merge(const FrameDesc& f, int b) {
+__device__ void border_merge(const FrameDesc& f, int b, int* hook) {
     const int limit = f.iter_limit > 0 ? f.iter_limit : kDefaultIterLimit;
     // root pairs this block has united during this merge (a cache: a collision only
     // costs a repeated union)
@@ -1012,20 +1012,20 @@ __device__ void border_merge(const FrameDesc& f, int b) {
     __syncthreads();
     const int W = min(f.strip_w, f.cols - b * f.strip_w);
     if (W < f.skip) {
-        border_merge_narrow(f, limit);
-        if (f.kd) border_merge_narrow_diag(f, limit);
+        border_merge_narrow(f, hook, limit);
+        if (f.kd) border_merge_narrow_diag(f, hook, limit);
         return;
     }
-    if (f.kd) border_merge_diag(f, b, limit, pair_set);
+    if (f.kd) border_merge_diag(f, hook, b, limit, pair_set);
     switch (f.skip) {
-        case 1: border_merge_s<1>(f, b, limit, pair_set); break;
-        case 2: border_merge_s<2>(f, b, limit, pair_set); break;
-        case 3: border_merge_s<3>(f, b, limit, pair_set); break;
-        case 4: border_merge_s<4>(f, b, limit, pair_set); break;
-        case 5: border_merge_s<5>(f, b, limit, pair_set); break;
-        case 6: border_merge_s<6>(f, b, limit, pair_set); break;
-        case 7: border_merge_s<7>(f, b, limit, pair_set); break;
-        default: border_merge_s<8>(f, b, limit, pair_set); break;
+        case 1: border_merge_s<1>(f, hook, b, limit, pair_set); break;
+        case 2: border_merge_s<2>(f, hook, b, limit, pair_set); break;
+        case 3: border_merge_s<3>(f, hook, b, limit, pair_set); break;
+        case 4: border_merge_s<4>(f, hook, b, limit, pair_set); break;
+        case 5: border_merge_s<5>(f, hook, b, limit, pair_set); break;
+        case 6: border_merge_s<6>(f, hook, b, limit, pair_set); break;
+        case 7: border_merge_s<7>(f, hook, b, limit, pair_set); break;
+        default: border_merge_s<8>(f, hook, b, limit, pair_set); break;
     }
 }
 
@@ -1075,8 +1075,9 @@ __device__ __forceinline__ void phase3_counts(int32_t* labels, int32_t* cnt, uin
     }
 }
 
+// r0: the first row that can change (rows above the topmost hooked root keep their labels).
 template <bool kCount>
-__device__ void phase3_strip(const FrameDesc& f, int si, unsigned long long* cache) {
+__device__ void phase3_strip(const FrameDesc& f, int si, unsigned long long* cache, int r0) {
     constexpr int G = 4;
     const int lane = threadIdx.x & 31;
     const int warp = threadIdx.x >> 5;
@@ -1092,15 +1093,16 @@ __device__ void phase3_strip(const FrameDesc& f, int si, unsigned long long* cac
     for (unsigned i = threadIdx.x; i < cn; i += blockDim.x) cache[i] = ~0ull;
     __syncthreads();
     const int nchunk = (W + 127) >> 7;
-    const int items = f.rows * nchunk;
+    const int items = (f.rows - r0) * nchunk;
     int last_l = -1, last_root = -1;
     for (int i0 = warp * G; i0 < items; i0 += nwarps * G) {
         int v[G][4];
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int it = i0 + g;
-            const int r = it / nchunk;
-            const int c = ((it - r * nchunk) << 7) + lane * 4;
+            const int rr = it / nchunk;
+            const int c = ((it - rr * nchunk) << 7) + lane * 4;
+            const int r = r0 + rr;
             const int32_t* row = f.labels + (size_t)r * f.cols + c0;
             if (it < items && vec && c + 4 <= W) {
                 const int4 x = __ldcg(reinterpret_cast<const int4*>(row + c));
@@ -1115,8 +1117,9 @@ __device__ void phase3_strip(const FrameDesc& f, int si, unsigned long long* cac
         for (int g = 0; g < G; ++g) {
             const int it = i0 + g;
             if (it >= items) break;
-            const int r = it / nchunk;
-            const int c = ((it - r * nchunk) << 7) + lane * 4;
+            const int rr = it / nchunk;
+            const int c = ((it - rr * nchunk) << 7) + lane * 4;
+            const int r = r0 + rr;
             bool changed = false;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
@@ -1176,6 +1179,7 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
     __shared__ int task_sh;
     __shared__ int flag_sh;
     __shared__ int merge_sh[2];
+    __shared__ int p3_row_sh;
     if (threadIdx.x == 0) mbar_init(&tma_bar, 1);
     __syncthreads();
     uint32_t parity = 0;
@@ -1238,7 +1242,7 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
                     const int bb = merge_sh[side] - 1;
                     if (bb < 0) continue;  // uniform
                     __threadfence();
-                    border_merge(f, bb);
+                    border_merge(f, bb, done_ctr + kCtrHookRows);
                     __threadfence();
                     __syncthreads();
                     if (threadIdx.x == 0) red_release_add(done_ctr, 1);
@@ -1257,9 +1261,13 @@ __global__ void __launch_bounds__(512, 2) flic_label_kernel(const LabelLaunch L)
                         break;
                     }
                 }
+                // the topmost row that a merge hooked a root of (the merges are all done)
+                p3_row_sh = f.rows - __ldcg(done_ctr + kCtrHookRows + si);
             }
             __syncthreads();
-            if (flag_sh) phase3_strip<kCount>(f, si, reinterpret_cast<unsigned long long*>(smem_raw));
+            if (flag_sh)
+                phase3_strip<kCount>(f, si, reinterpret_cast<unsigned long long*>(smem_raw),
+                                     p3_row_sh);
         }
         __syncthreads();  // shared memory is reused by the next task
     }

@@ -70,6 +70,7 @@ constexpr int kCtrExit = 1;
 constexpr int kCtrFrames = 2;
 constexpr int kCtrHookRows = 2 + kMaxStrips;
 constexpr int kCtrPerFrame = 2 + 2 * kMaxStrips;
+static_assert(kCtrHookRows + kMaxStrips <= kCtrPerFrame, "hook rows inside the frame's counters");
 __host__ __device__ inline size_t counter_ints(int nframes) {
     return size_t(kCtrFrames) + size_t(kCtrPerFrame) * size_t(nframes);
 }

@@ -228,3 +228,35 @@ def test_changing_frame_sets_regrow_the_scratch(flic):
                     h.close()
     finally:
         b.close()
+
+
+def test_hooked_rows_only_low_in_the_frame(flic):
+    """Components that cross strip borders only low in the frame (a full bottom row, a
+    two-row band in the middle) under components that stay inside one strip: the flatten
+    of each strip starts at its topmost hooked root, and the labels above it (plain and
+    fused calls, with and without wrap) still equal the oracle's."""
+    R, C = 16, 512
+    elev = np.radians(np.linspace(10.0, -10.0, R))
+    rng = np.zeros((R, C), np.float32)
+    rng[0:4, 10:21] = 5.0       # inside the first strip
+    rng[5:9, 300:310] = 5.0     # inside a middle strip
+    rng[6:8, 100:200] = 5.0     # crosses the border between the first two strips
+    rng[15, :] = 5.0            # the bottom row crosses every border
+    for wrap in (True, False):
+        hs = [flic.flic_create(R, C, elev, 2 * np.pi / C, 50.0, 1, wrap=wrap)]
+        b = flic.flic_batch_create(1)
+        try:
+            flic.flic_batch_set_tuning(b, 2048, 128, 64, 0)  # 128-column strips
+            ref = oracle.label(rng, elev, 2 * np.pi / C, 50.0, 1, wrap)
+            r = torch.from_numpy(rng.reshape(-1)).to(DEV)
+            lab = torch.full((R * C,), 777, dtype=torch.int32, device=DEV)
+            flic.flic_label_batch(b, flic.BatchArgs(hs, [r], [lab]))
+            torch.cuda.synchronize()
+            assert flic.flic_batch_last_plan(b)["strips"] == 4
+            assert np.array_equal(lab.cpu().numpy(), ref.reshape(-1)), wrap
+            got, nums = _fused(flic, b, hs, [rng], 1)
+            _check(got, nums, [oracle.filter_relabel(ref, 1)])
+        finally:
+            b.close()
+            for h in hs:
+                h.close()
